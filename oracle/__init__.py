@@ -1,0 +1,11 @@
+"""FP64 CPU oracle of the semi-Lagrangian lattice Boltzmann step.
+
+TEST INFRASTRUCTURE ONLY: plain, slow, obviously correct numpy code written
+from the paper (arXiv:2101.03982).  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it; the product path (the
+CUDA library and its binding) never does, and the oracle imports nothing from
+the product.
+
+Parity unpinned: ``sllbm.strain_dissipation`` (a builder's estimator with no
+formula in the paper) is checked only for agreement with the CUDA path.
+"""

@@ -1,0 +1,142 @@
+"""Pins of the oracle's whole step (Sec. 3: pull, moments, equilibrium, BGK).
+
+* On-lattice special case: D2Q9 with c_s^2 = 1/3 and dt = dx equals the
+  textbook stream-and-collide LBM with numpy.roll (Sec. 5 names numpy.roll).
+* Conservation of mass, momentum and (compressible) total energy on a
+  periodic grid; a uniform equilibrium is a fixed point; the temperature
+  relation returns the temperature an equilibrium was built with.
+* 2D Taylor-Green vortex: amplitude decays as exp(-2 nu t).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sllbm as O
+from oracle import velocity_sets as V
+
+
+def perturbed_state(prm, grid, seed, amp=1e-3):
+    rng = np.random.default_rng(seed)
+    D = prm.vs.D
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1, grid)
+    u = 0.05 * prm.vs.cs * rng.uniform(-1, 1, (D,) + grid)
+    theta = 1.0 + 0.1 * rng.uniform(-1, 1, grid) if prm.compressible else None
+    f, g = O.init_equilibrium(prm, rho, u, theta)
+    f = f * (1.0 + amp * rng.uniform(-1, 1, f.shape))
+    if g is not None:
+        g = g * (1.0 + amp * rng.uniform(-1, 1, g.shape))
+    return f, g
+
+
+def textbook_d2q9_step(f, tau):
+    """Stream with numpy.roll, then collide with the D2Q9 BGK equilibrium."""
+    c = np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [1, 1], [-1, 1], [0, -1], [1, -1], [-1, -1]])
+    w = np.array([4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 9, 1 / 36, 1 / 36])
+    fs = np.stack([np.roll(np.roll(f[i], c[i][0], axis=1), c[i][1], axis=0) for i in range(9)])
+    rho = fs.sum(0)
+    ux = (c[:, 0, None, None] * fs).sum(0) / rho
+    uy = (c[:, 1, None, None] * fs).sum(0) / rho
+    cu = c[:, 0, None, None] * ux + c[:, 1, None, None] * uy
+    feq = w[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (ux ** 2 + uy ** 2))
+    return fs - (fs - feq) / tau
+
+
+def test_on_lattice_case_equals_roll_lbm():
+    vs = V.get("D2Q9").scaled(1.0 / math.sqrt(3.0))
+    # velocity order of this build: i = ix + 3 iy over nodes [0, +1, -1]
+    order = np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [1, 1], [-1, 1], [0, -1], [1, -1], [-1, -1]])
+    assert np.allclose(vs.xi, order)
+    prm = O.Params(vs, 2, 3, dt=0.1, dx=0.1, tau=0.8)
+    f, _ = perturbed_state(prm, (12, 10), 1, amp=1e-2)
+    got, _, _ = O.step(prm, f)
+    want = textbook_d2q9_step(f, 0.8)
+    assert np.allclose(got, want, atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("name,N,comp,p", [("D3Q27", 2, False, 3), ("D3Q13", 2, False, 4),
+                                            ("D2Q25", 4, True, 4), ("D3Q45", 4, True, 3)])
+def test_conservation(name, N, comp, p):
+    vs = V.get(name)
+    grid = (6, 7, 8)[:vs.D][::-1] if vs.D == 3 else (9, 10)
+    max_xi = np.abs(vs.xi).max()
+    dx = 0.1
+    dt = 0.37 * dx / max_xi
+    prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=0.7, compressible=comp, gamma=1.4, mu=0.01)
+    f, g = perturbed_state(prm, grid, 2)
+    fn, gn, _ = O.step(prm, f, g)
+
+    def totals(f, g):
+        ff = f.reshape(vs.Q, -1)
+        mass = ff.sum()
+        mom = vs.xi.T @ ff.sum(1)
+        e = ((vs.xi ** 2).sum(1) * ff.sum(1)).sum() + (g.sum() if g is not None else 0.0)
+        return mass, mom, e
+
+    m0, p0, e0 = totals(f, g)
+    m1, p1, e1 = totals(fn, gn)
+    assert abs(m1 - m0) < 1e-13 * m0
+    assert np.abs(p1 - p0).max() < 1e-13 * m0
+    if comp:
+        assert abs(e1 - e0) < 1e-13 * e0
+
+
+@pytest.mark.parametrize("name,N,comp", [("D3Q21", 2, False), ("D2Q19", 4, True)])
+def test_uniform_equilibrium_is_fixed_point(name, N, comp):
+    vs = V.get(name)
+    grid = (5, 6, 7) if vs.D == 3 else (8, 9)
+    prm = O.Params(vs, N, 4, dt=0.01, dx=0.05, tau=0.9, compressible=comp, mu=0.02)
+    rho = np.full(grid, 1.1)
+    u = np.stack([np.full(grid, 0.03 * (a + 1)) for a in range(vs.D)])
+    theta = np.full(grid, 1.2) if comp else None
+    f, g = O.init_equilibrium(prm, rho, u, theta)
+    fn, gn, _ = O.step(prm, f, g)
+    assert np.allclose(fn, f, atol=1e-15, rtol=1e-13)
+    if comp:
+        assert np.allclose(gn, g, atol=1e-15, rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["D2Q19", "D2Q25", "D3Q45"])
+def test_temperature_round_trip(name):
+    vs = V.get(name)
+    grid = (4, 5, 6) if vs.D == 3 else (7, 8)
+    prm = O.Params(vs, 4, 3, dt=0.01, dx=0.05, compressible=True, gamma=1.4, mu=0.01)
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.6, 1.8, grid)
+    u = rng.uniform(-0.5, 0.5, (vs.D,) + grid)
+    theta = rng.uniform(0.5, 2.0, grid)
+    f, g = O.init_equilibrium(prm, rho, u, theta)
+    r2, u2, t2 = O.moments_of_state(prm, f, g)
+    assert np.allclose(r2, rho, rtol=1e-13)
+    assert np.allclose(u2, u, atol=1e-13)
+    assert np.allclose(t2, theta, rtol=1e-12)
+
+
+def tgv_amplitude_error(n, steps=200):
+    vs = V.get("D2Q9").scaled(1.0 / math.sqrt(3.0))
+    u0, Re = 0.05, 100.0
+    dx = 2 * np.pi / n
+    dt = 0.4 * dx
+    nu = u0 / Re
+    tau = O.tau_isothermal(nu, vs.cs, dt)
+    prm = O.Params(vs, 2, 3, dt=dt, dx=dx, tau=tau)
+    x = np.arange(n) * dx
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    u = np.stack([u0 * np.sin(X) * np.cos(Y), -u0 * np.cos(X) * np.sin(Y)])
+    # pressure balancing u.grad(u) for this velocity field: p' = +(u0^2/4)(cos 2x + cos 2y)
+    rho = 1.0 + (u0 ** 2 / 4.0) * (np.cos(2 * X) + np.cos(2 * Y)) / vs.cs ** 2
+    f, _ = O.init_equilibrium(prm, rho, u)
+    for _ in range(steps):
+        f, _, diag = O.step(prm, f)
+    _, uu, _ = O.moments_of_state(prm, f)
+    amp = 4.0 * (uu[0] * np.sin(X) * np.cos(Y)).mean() / u0
+    exact = math.exp(-2.0 * nu * steps * dt)
+    return abs(amp / exact - 1.0), diag
+
+
+def test_tgv2d_decay():
+    e64, diag = tgv_amplitude_error(64)
+    assert e64 < 1e-3
+    e128, _ = tgv_amplitude_error(128, steps=400)
+    assert e128 < e64
+    assert diag["k"] > 0
