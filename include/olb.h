@@ -1,0 +1,177 @@
+/*
+ * olb.h -- C ABI of the GB300 semi-Lagrangian off-lattice Boltzmann library.
+ *
+ * The library advances the populations of one velocity set on a uniform,
+ * periodic Cartesian grid by the semi-Lagrangian lattice Boltzmann step of
+ * Wilde et al., "Cubature rules for weakly and fully compressible off-lattice
+ * Boltzmann methods" (arXiv:2101.03982), Sec. 3:
+ *
+ *   1. pull: every population f_i is interpolated at the departure point
+ *      x - xi_i dt (Sec. 3, Eq. sl_streaming) with a tensor product of
+ *      equidistant Lagrange polynomials of degree p (one fixed stencil per
+ *      velocity, because every node of a uniform grid has the same offset);
+ *   2. moments rho = sum f_i, rho u = sum xi_i f_i (Sec. 3, Eqs. density and
+ *      momentum); compressible runs add 2 rho C_v theta = sum |xi_i-u|^2 f_i/T0
+ *      + sum g_i (Sec. 3, temperature relation);
+ *   3. Hermite equilibrium of order N (Sec. 3 and Appendix A);
+ *   4. BGK relaxation f <- f - (f - f^eq)/tau (Sec. 3, LBE), with
+ *      tau = mu/(c_s^2 dt P) + 1/2, P = rho theta, per node when compressible.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Layout: a scalar field is [nz][ny][nx], x fastest (2D: nz = 1).  A vector
+ *   field u is structure-of-arrays [D][nz][ny][nx].  Populations are planes
+ *   [plane][nz][ny][nx]; planes 0..Q-1 hold f_i in the order of the paper's
+ *   tables, planes Q..2Q-1 hold g_i in compressible runs.
+ * - "on_device": 1 means the pointer is CUDA device memory that the call uses
+ *   on the handle's stream (for example a torch tensor's data_ptr()); 0 means
+ *   host memory, copied synchronously inside the call.
+ * - Ownership: the handle owns its population buffers, scratch and tables.
+ *   Caller buffers are only read or written during the call that gets them.
+ * - Errors: every int-returning call returns OLB_OK (0) or a negative code
+ *   below; nothing aborts and nothing throws.  olb_last_error() describes the
+ *   most recent failure of the calling thread.  A handle is used by one host
+ *   thread at a time.
+ * - Units: lengths in units of the domain (dx = grid spacing), times in the
+ *   units of dt; the velocity set's abscissae are scaled by cs_scale.
+ */
+#ifndef OLB_H
+#define OLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OLB_OK 0
+#define OLB_EINVAL (-1)         /* invalid argument */
+#define OLB_ENOMEM (-2)         /* device or host allocation failed */
+#define OLB_ECUDA (-3)          /* a CUDA runtime call failed */
+#define OLB_ENONFINITE (-4)     /* the state holds NaN or Inf */
+#define OLB_ETIMEOUT (-5)       /* a bounded host wait ran out */
+#define OLB_EBOUNDS (-6)        /* a size or index lies outside what the call supports */
+#define OLB_EUNSUPPORTED (-7)   /* combination not built or not exact (e.g. N too high) */
+#define OLB_ESTATE (-8)         /* call out of order (e.g. no step yet) */
+
+/* Velocity sets (Sec. 2, Table 1; Tables 2-3; Appendices C-E). */
+typedef enum {
+  OLB_D2Q9 = 0,   /* Gauss-Hermite product of D1Q3, degree 5, c_s = 1 */
+  OLB_D2Q19 = 1,  /* Haegemans-Piessens cubature, degree 9 (Appendix C) */
+  OLB_D2Q25 = 2,  /* Gauss-Hermite product of D1Q5, degree 9 */
+  OLB_D3Q13 = 3,  /* icosahedron, degree 5 (Table 2) */
+  OLB_D3Q21 = 4,  /* dodecahedron, degree 5, c_s = sqrt(3/5) (Table 3) */
+  OLB_D3Q27 = 5,  /* Gauss-Hermite product of D1Q3, degree 5 */
+  OLB_D3V27 = 6,  /* Stroud-Secrest, degree 7 (Appendix D) */
+  OLB_D3Q45 = 7   /* Konyaev cubature, degree 9 (Appendix E) */
+} olb_velocity_set;
+
+/* Storage of the populations.  Shifted storage keeps f_i - w_i rho0 (and
+ * g_i - w_i (2C_v - D) rho0), rounded to nearest even; the arithmetic of the
+ * step is then FP32.  OLB_FP64 stores f_i itself and computes in FP64. */
+typedef enum {
+  OLB_FP64 = 0,
+  OLB_FP32_SHIFTED = 1,
+  OLB_BF16_SHIFTED = 2,
+  OLB_FP16_SHIFTED = 3
+} olb_storage;
+
+/* Periodic grid: dim in {2,3}; n[2] must be 1 when dim == 2; dx > 0. */
+typedef struct {
+  int dim;
+  int n[3];
+  double dx;
+} olb_grid;
+
+typedef struct {
+  int interp_order;  /* p, Lagrange degree per axis; built: 1..6 (FP64), 2..4 (others) */
+  int storage;       /* olb_storage */
+  double cs_scale;   /* abscissae and c_s scaled by this factor (D2Q9 with c_s^2=1/3: 1/sqrt(3)) */
+  int compressible;  /* 0: theta = 1, f only; 1: f and g, per-node tau(P) (requires c_s = 1) */
+  double gamma;      /* heat capacity ratio (compressible), C_v = 1/(gamma-1) */
+  double mu;         /* dynamic viscosity (compressible; the tau argument is then ignored) */
+  double rho0;       /* reference density of the shifted storage (default 1) */
+  int allow_inexact; /* 1: accept a quadrature degree below 2N */
+  void* stream;      /* cudaStream_t for every call of the handle; NULL = default stream */
+} olb_options;
+
+typedef struct olb_ctx* olb_handle;
+
+/* Fill *opt with defaults: p = 3, FP64, cs_scale = 1, isothermal, gamma = 1.4,
+ * mu = 0, rho0 = 1, allow_inexact = 0, stream = NULL. */
+void olb_default_options(olb_options* opt);
+
+/* Abscissae count Q, dimension D, c_s, largest |xi_{i,alpha}| and degree of a
+ * velocity set, unscaled.  Any pointer may be NULL.  No GPU needed. */
+int olb_velocity_set_info(int velocity_set, int* Q, int* D, double* cs,
+                          double* max_abs_xi, int* degree);
+
+/* Copy the velocity set's abscissae (Q x D, row-major, unscaled) and weights. */
+int olb_velocity_set_table(int velocity_set, double* xi, double* w);
+
+/* Create a simulation.  hermite_order N in {2,3,4} (Sec. 3); tau > 1/2 the
+ * BGK relaxation time (ignored when compressible: tau(P) from opt->mu); dt > 0.
+ * Allocates the two population buffers, the per-CTA scratch and the reduction
+ * buffers on the current CUDA device.  Returns OLB_EUNSUPPORTED when the set's
+ * degree is below 2N (the exactness rule d >= N + M of Sec. 2 with M = N)
+ * unless allow_inexact is set. */
+int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double tau,
+               double dt, const olb_options* opt /* nullable */, olb_handle* out);
+
+int olb_destroy(olb_handle h);
+
+/* Q, planes (Q or 2Q), nodes, dimension and the storage element size in bytes. */
+int olb_shape(olb_handle h, int* Q, int* planes, size_t* nodes, int* dim, int* elem_bytes);
+
+/* Per-velocity stencil table used by the pull: m0[Q*3] (first support point
+ * per axis, grid units) and W[Q*3*(p+1)] Lagrange weights (FP64). */
+int olb_stencil(olb_handle h, int* m0, double* W);
+
+/* f = f^eq(rho, u, theta) (and g = theta (2 C_v - D) f^eq): rho [n], u [D][n],
+ * theta [n] or NULL (= 1).  FP64 fields. */
+int olb_init_fields(olb_handle h, const double* rho, const double* u, const double* theta,
+                    int on_device);
+
+/* Advance n >= 0 steps (pull, then collide).  Asynchronous on the handle's
+ * stream.  Each step also leaves per-CTA FP64 partial sums of the global
+ * reductions, which olb_reductions() combines. */
+int olb_step(olb_handle h, int n);
+
+/* rho [n], u [D][n], theta [n] (nullable) of the stored post-collision state. */
+int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_device);
+
+/* Global sums of the most recent step (or of the stored state when no step
+ * has run since it was set), in a fixed summation order:
+ *   out[0] k     = mean |u|^2/2                       (Sec. 4.2, kinetic energy)
+ *   out[1] k_rho = mean rho |u|^2/2
+ *   out[2] eps   = mean 2 nu S:S, S = -Pi_neq/(2 P tau dt) (estimator; NaN without a step)
+ *   out[3] mass  = sum rho
+ *   out[4..6]    = sum rho u (x, y, z)
+ *   out[7]       = number of nodes with non-finite rho, u or theta
+ * Synchronises the stream.  Returns OLB_ENONFINITE (after filling out) when
+ * out[7] > 0. */
+int olb_reductions(olb_handle h, double out[8]);
+
+/* k and (nullable) the dissipation estimate; a view of olb_reductions(). */
+int olb_kinetic_energy(olb_handle h, double* k, double* dissipation);
+
+/* Populations as FP64 unshifted values, [planes][n]. */
+int olb_get_populations(olb_handle h, double* f, int on_device);
+int olb_set_populations(olb_handle h, const double* f, int on_device);
+
+/* Raw stored state (checkpoint): exactly olb_state_bytes() bytes. */
+size_t olb_state_bytes(olb_handle h);
+int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device);
+int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);
+
+/* Wait for the handle's stream, polling with a bound of timeout_ms (<= 0: no bound). */
+int olb_synchronize(olb_handle h, int timeout_ms);
+
+/* Message for an error code, and the calling thread's most recent failure. */
+const char* olb_strerror(int code);
+const char* olb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OLB_H */

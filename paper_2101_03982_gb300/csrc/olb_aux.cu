@@ -1,0 +1,210 @@
+// Auxiliary kernels around the fused step: equilibrium initialisation from
+// macroscopic fields (Sec. 3 equilibrium with Appendix A moments), moments of
+// a stored state, FP64 <-> storage conversion, and the fixed-order final sum
+// of the per-CTA reduction partials.  None of them is on the per-step path.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <type_traits>
+
+#include "olb_internal.h"
+#include "olb_step.cuh"
+
+namespace olb {
+
+namespace {
+
+template <typename S>
+__device__ __forceinline__ S from_double(double v);
+template <>
+__device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <>
+__device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
+
+template <typename S>
+__device__ __forceinline__ double to_double(S v) { return (double)Store<S>::ld(v); }
+
+constexpr int AUX_NT = 256;
+
+template <typename S>
+__global__ void __launch_bounds__(AUX_NT) init_kernel(const __grid_constant__ AuxArgs a, S* state, const double* rho,
+                                                   const double* u, const double* theta) {
+  const long long n = a.nnodes;
+  const bool comp = a.compressible != 0;
+  for (long long node = blockIdx.x * (long long)AUX_NT + threadIdx.x; node < n;
+       node += (long long)gridDim.x * AUX_NT) {
+    const double r = rho ? rho[node] : a.rest_rho;
+    const double ux = rho ? u[node] : 0.0, uy = rho ? u[n + node] : 0.0;
+    const double uz = (rho && a.D == 3) ? u[2 * n + node] : 0.0;
+    const double th = (comp && theta) ? theta[node] : 1.0;
+    const double uhx = ux * a.inv_cs, uhy = uy * a.inv_cs, uhz = uz * a.inv_cs;
+    const double q = uhx * uhx + uhy * uhy + uhz * uhz;
+    const double t = th - 1.0;
+    const double A = r - a.rho_ref;
+    const double rth = r * th, gA = r * t + A;
+    for (int i = 0; i < a.Q; ++i) {
+      const double xr = a.xih[i][0] * a.xih[i][0] + a.xih[i][1] * a.xih[i][1] + a.xih[i][2] * a.xih[i][2];
+      const double rD = xr - a.D, rp = xr * xr - 2.0 * (a.D + 2) * xr + a.D * (a.D + 2.0);
+      const double s = a.xih[i][0] * uhx + a.xih[i][1] * uhy + a.xih[i][2] * uhz;
+      const double ph = comp ? phi_m1<double, true>(s, q, t, rD, rp, a.N) : phi_m1<double, false>(s, q, t, rD, rp, a.N);
+      state[(long long)i * n + node] = from_double<S>(a.w[i] * (A + r * ph));
+      if (comp) state[(long long)(a.Q + i) * n + node] = from_double<S>(a.w[i] * a.gfac * (gA + rth * ph));
+    }
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(AUX_NT) moments_kernel(const __grid_constant__ AuxArgs a, const S* state, double* rho,
+                                                      double* u, double* theta, double* partials) {
+  const long long n = a.nnodes;
+  const bool comp = a.compressible != 0;
+  double red[NRED];
+  for (int q = 0; q < NRED; ++q) red[q] = 0.0;
+  for (long long node = blockIdx.x * (long long)AUX_NT + threadIdx.x; node < n;
+       node += (long long)gridDim.x * AUX_NT) {
+    double A = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, B = 0.0, G = 0.0;
+    for (int i = 0; i < a.Q; ++i) {
+      const double v = to_double(state[(long long)i * n + node]);
+      A += v;
+      jx += a.xi[i][0] * v;
+      jy += a.xi[i][1] * v;
+      jz += a.xi[i][2] * v;
+      B += (a.xi[i][0] * a.xi[i][0] + a.xi[i][1] * a.xi[i][1] + a.xi[i][2] * a.xi[i][2]) * v;
+      if (comp) G += to_double(state[(long long)(a.Q + i) * n + node]);
+    }
+    const double r = a.rho_ref + A;
+    const double ux = jx / r, uy = jy / r, uz = jz / r;
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    double th = 1.0;
+    if (comp) th = 1.0 + (B + G - r * u2 - a.two_cv * A) / (a.two_cv * r);
+    if (rho) rho[node] = r;
+    if (u) {
+      u[node] = ux;
+      u[n + node] = uy;
+      if (a.D == 3) u[2 * n + node] = uz;
+    }
+    if (theta) theta[node] = th;
+    red[0] += 0.5 * u2;
+    red[1] += 0.5 * r * u2;
+    red[3] += r;
+    red[4] += jx;
+    red[5] += jy;
+    red[6] += jz;
+    red[7] += (isfinite(r) && isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(th)) ? 0.0 : 1.0;
+  }
+  if (!partials) return;
+  __shared__ double sm[AUX_NT / 32][NRED];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < NRED; ++q) {
+    double v = red[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    double s = 0.0;
+    for (int w = 0; w < AUX_NT / 32; ++w) s += sm[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * NRED + threadIdx.x] = s;
+  }
+}
+
+template <typename S>
+__global__ void to_f64_kernel(const __grid_constant__ AuxArgs a, const S* state, double* f) {
+  const long long total = (long long)a.planes * a.nnodes;
+  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
+    const int p = (int)(e / a.nnodes);
+    f[e] = to_double(state[e]) + a.base[p];
+  }
+}
+
+template <typename S>
+__global__ void from_f64_kernel(const __grid_constant__ AuxArgs a, S* state, const double* f) {
+  const long long total = (long long)a.planes * a.nnodes;
+  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
+    const int p = (int)(e / a.nnodes);
+    state[e] = from_double<S>(f[e] - a.base[p]);
+  }
+}
+
+__global__ void __launch_bounds__(256) reduce_final_kernel(const double* partials, int nslots, double* out) {
+  __shared__ double sm[256];
+  for (int q = 0; q < NRED; ++q) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nslots; k += 256) s += partials[(size_t)k * NRED + q];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sm[0];
+    __syncthreads();
+  }
+}
+
+int aux_grid(long long work) {
+  long long g = (work + AUX_NT - 1) / AUX_NT;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename F>
+int by_storage(int storage, F&& f) {
+  switch (storage) {
+    case 0: return f((double*)nullptr);
+    case 1: return f((float*)nullptr);
+    case 2: return f((__nv_bfloat16*)nullptr);
+    case 3: return f((__half*)nullptr);
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+int launch_init_fields(const AuxArgs& a, void* state, const double* rho, const double* u, const double* theta,
+                       void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    init_kernel<S><<<aux_grid(a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, rho, u, theta);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_state_moments(const AuxArgs& a, const void* state, double* rho, double* u, double* theta,
+                         double* partials, int grid, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    moments_kernel<S><<<grid, AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state, rho, u, theta, partials);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_to_f64(const AuxArgs& a, const void* state, double* f, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    to_f64_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state, f);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    from_f64_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, f);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_reduce_final(const double* partials, int nslots, double* out, void* stream) {
+  reduce_final_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(partials, nslots, out);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace olb

@@ -1,0 +1,688 @@
+// C ABI of the library (include/olb.h): handle lifetime, argument checks,
+// stencil and table set-up on the host, and dispatch of the kernels.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/olb.h"
+#include "olb_internal.h"
+
+using namespace olb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(OLB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct olb_ctx {
+  olb_grid grid{};
+  int vs_id = 0, N = 2, p = 3, storage = 0, comp = 0, allow_inexact = 0;
+  double tau = 1.0, dt = 0.0, gamma = 1.4, mu = 0.0, rho0 = 1.0, cs = 1.0, cs_scale = 1.0;
+  VelocitySet set{};  // scaled abscissae
+  int Q = 0, planes = 0, D = 0, elem = 8;
+  long long nnodes = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* scratch = nullptr;
+  double* partials = nullptr;
+  double* red_dev = nullptr;
+  int step_grid = 0, partial_slots = 0;
+  int partials_from_step = 0;  // 1: the partials hold the last step's sums
+  int have_partials = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  StepInfo info{};
+  StepArgs args{};
+  std::vector<unsigned char> veltab, stentab;
+  AuxArgs aux{};
+  std::vector<int> m0;        // [Q][3], oracle convention on every axis
+  std::vector<double> W;      // [Q][3][p+1]
+};
+
+namespace {
+
+int storage_bytes(int storage) {
+  switch (storage) {
+    case OLB_FP64: return 8;
+    case OLB_FP32_SHIFTED: return 4;
+    case OLB_BF16_SHIFTED:
+    case OLB_FP16_SHIFTED: return 2;
+    default: return 0;
+  }
+}
+
+int step_info(int D, int P, int storage, int comp, StepInfo* out) {
+  switch (storage) {
+    case OLB_FP64: return step_info_f64(D, P, comp, out);
+    case OLB_FP32_SHIFTED: return step_info_f32(D, P, comp, out);
+    case OLB_BF16_SHIFTED: return step_info_bf16(D, P, comp, out);
+    case OLB_FP16_SHIFTED: return step_info_f16(D, P, comp, out);
+    default: return -1;
+  }
+}
+
+// Lagrange stencil of degree p around offset delta (grid units): first point
+// m0 and weights W[j] = prod_{k != j} (delta - m_k) / (m_j - m_k).
+void lagrange_stencil(double delta, int p, int* m0, double* W) {
+  int first = (p % 2 == 1) ? (int)std::floor(delta) - (p - 1) / 2 : (int)std::floor(delta + 0.5) - p / 2;
+  *m0 = first;
+  for (int j = 0; j <= p; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k <= p; ++k)
+      if (k != j) prod *= (delta - (first + k)) / (double)((first + j) - (first + k));
+    W[j] = prod;
+  }
+}
+
+template <typename C>
+void fill_veltab(olb_ctx* h) {
+  h->veltab.assign(sizeof(VelTab<C>), 0);
+  auto* t = reinterpret_cast<VelTab<C>*>(h->veltab.data());
+  const int D = h->D;
+  for (int i = 0; i < h->Q; ++i) {
+    double xh[3], x2 = 0.0, r = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double x = h->set.xi[i][a];
+      xh[a] = x / h->cs;
+      t->xi[i][a] = (C)x;
+      t->xih[i][a] = (C)xh[a];
+      x2 += x * x;
+      r += xh[a] * xh[a];
+    }
+    t->w[i] = (C)h->set.w[i];
+    t->xi2[i] = (C)x2;
+    t->rD[i] = (C)(r - D);
+    t->rpoly[i] = (C)(r * r - 2.0 * (D + 2) * r + D * (D + 2.0));
+    const double* x = h->set.xi[i];
+    t->xx[i][0] = (C)(x[0] * x[0]);
+    t->xx[i][1] = (C)(x[1] * x[1]);
+    t->xx[i][2] = (C)(x[2] * x[2]);
+    t->xx[i][3] = (C)(x[0] * x[1]);
+    t->xx[i][4] = (C)(x[0] * x[2]);
+    t->xx[i][5] = (C)(x[1] * x[2]);
+  }
+}
+
+template <typename C, int P1>
+void fill_stentab_p(olb_ctx* h) {
+  h->stentab.assign(sizeof(StencilTab<C, P1>), 0);
+  auto* t = reinterpret_cast<StencilTab<C, P1>*>(h->stentab.data());
+  const int p = h->p;
+  for (int i = 0; i < h->Q; ++i) {
+    int act = 0;
+    for (int a = 0; a < h->D; ++a) {
+      if (h->set.xi[i][a] != 0.0) act |= 1 << a;
+      t->m0[i][a] = h->m0[i * 3 + a];
+      for (int j = 0; j <= p; ++j) t->W[i][a][j] = (C)h->W[(i * 3 + a) * (p + 1) + j];
+    }
+    t->active[i] = act;
+  }
+}
+
+template <typename C>
+void fill_stentab(olb_ctx* h) {
+  switch (h->p) {
+    case 1: fill_stentab_p<C, 2>(h); break;
+    case 2: fill_stentab_p<C, 3>(h); break;
+    case 3: fill_stentab_p<C, 4>(h); break;
+    case 4: fill_stentab_p<C, 5>(h); break;
+    case 5: fill_stentab_p<C, 6>(h); break;
+    case 6: fill_stentab_p<C, 7>(h); break;
+  }
+}
+
+void release(olb_ctx* h) {
+  if (!h) return;
+  for (int k = 0; k < 2; ++k)
+    if (h->buf[k]) cudaFree(h->buf[k]);
+  if (h->scratch) cudaFree(h->scratch);
+  if (h->partials) cudaFree(h->partials);
+  if (h->red_dev) cudaFree(h->red_dev);
+  delete h;
+}
+
+int set_device(olb_ctx* h) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != h->device) {
+    e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  return OLB_OK;
+}
+
+int stream_sync(olb_ctx* h, int timeout_ms) {
+  if (timeout_ms <= 0) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? OLB_OK : cuda_fail(e, "cudaStreamSynchronize");
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(h->stream);
+    if (e == cudaSuccess) return OLB_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+    auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) return fail(OLB_ETIMEOUT, "stream did not finish within the time limit");
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+// Copy `bytes` between a caller buffer and a device buffer on the stream;
+// host copies are completed before returning.
+int copy_in(olb_ctx* h, void* dev_dst, const void* src, size_t bytes, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dev_dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  return on_device ? OLB_OK : stream_sync(h, 0);
+}
+
+int copy_out(olb_ctx* h, void* dst, const void* dev_src, size_t bytes, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, dev_src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  return on_device ? OLB_OK : stream_sync(h, 0);
+}
+
+// Device staging buffer for host-side FP64 arrays (freed by the caller).
+int dev_alloc(olb_ctx* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
+  if (e != cudaSuccess) return fail(OLB_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  return OLB_OK;
+}
+
+int launch_rc(int rc, const char* what) {
+  if (rc == 0) return OLB_OK;
+  if (rc < 0) return fail(OLB_EUNSUPPORTED, std::string(what) + ": configuration not built");
+  return cuda_fail((cudaError_t)rc, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+void olb_default_options(olb_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->interp_order = 3;
+  opt->storage = OLB_FP64;
+  opt->cs_scale = 1.0;
+  opt->compressible = 0;
+  opt->gamma = 1.4;
+  opt->mu = 0.0;
+  opt->rho0 = 1.0;
+  opt->allow_inexact = 0;
+  opt->stream = nullptr;
+}
+
+int olb_velocity_set_info(int velocity_set, int* Q, int* D, double* cs, double* max_abs_xi, int* degree) {
+  VelocitySet vs;
+  if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
+  double m = 0.0;
+  for (int i = 0; i < vs.Q; ++i)
+    for (int a = 0; a < 3; ++a) m = std::fmax(m, std::fabs(vs.xi[i][a]));
+  if (Q) *Q = vs.Q;
+  if (D) *D = vs.D;
+  if (cs) *cs = vs.cs;
+  if (max_abs_xi) *max_abs_xi = m;
+  if (degree) *degree = vs.degree;
+  return OLB_OK;
+}
+
+int olb_velocity_set_table(int velocity_set, double* xi, double* w) {
+  VelocitySet vs;
+  if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
+  for (int i = 0; i < vs.Q; ++i) {
+    if (xi)
+      for (int a = 0; a < vs.D; ++a) xi[i * vs.D + a] = vs.xi[i][a];
+    if (w) w[i] = vs.w[i];
+  }
+  return OLB_OK;
+}
+
+int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double tau, double dt,
+               const olb_options* opt_in, olb_handle* out) {
+  if (!grid || !out) return fail(OLB_EINVAL, "null grid or output handle");
+  *out = nullptr;
+  olb_options opt;
+  olb_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (grid->dim != 2 && grid->dim != 3) return fail(OLB_EINVAL, "grid dim must be 2 or 3");
+  if (grid->n[0] < 1 || grid->n[1] < 1 || grid->n[2] < 1) return fail(OLB_EINVAL, "grid sizes must be >= 1");
+  if (grid->dim == 2 && grid->n[2] != 1) return fail(OLB_EINVAL, "2D grid needs n[2] == 1");
+  if (!(grid->dx > 0.0) || !std::isfinite(grid->dx)) return fail(OLB_EINVAL, "dx must be positive");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OLB_EINVAL, "dt must be positive");
+  if (hermite_order < 2 || hermite_order > 4) return fail(OLB_EINVAL, "hermite_order must be 2, 3 or 4");
+  if (opt.interp_order < 1 || opt.interp_order > MAXP) return fail(OLB_EINVAL, "interp_order must be in 1..6");
+  if (storage_bytes(opt.storage) == 0) return fail(OLB_EINVAL, "unknown storage");
+  if (!(opt.cs_scale > 0.0) || !std::isfinite(opt.cs_scale)) return fail(OLB_EINVAL, "cs_scale must be positive");
+  if (!(opt.rho0 > 0.0)) return fail(OLB_EINVAL, "rho0 must be positive");
+
+  VelocitySet vs;
+  if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
+  if (vs.D != grid->dim) return fail(OLB_EINVAL, "velocity set dimension differs from the grid's");
+  if (vs.degree < 2 * hermite_order && !opt.allow_inexact)
+    return fail(OLB_EUNSUPPORTED, "quadrature degree below 2N: the equilibrium moments are not exact (d >= N + M)");
+  const double cs = vs.cs * opt.cs_scale;
+  if (opt.compressible) {
+    if (std::fabs(cs - 1.0) > 1e-12)
+      return fail(OLB_EUNSUPPORTED, "compressible runs need c_s = 1 (T0 = 1)");
+    if (!(opt.gamma > 1.0)) return fail(OLB_EINVAL, "gamma must exceed 1");
+    if (!(opt.mu > 0.0)) return fail(OLB_EINVAL, "compressible runs need mu > 0");
+  } else if (!(tau > 0.5) || !std::isfinite(tau)) {
+    return fail(OLB_EINVAL, "tau must exceed 1/2");
+  }
+  const long long nnodes = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  if (nnodes > (1LL << 31) - 1) return fail(OLB_EBOUNDS, "grid larger than 2^31 nodes");
+
+  olb_ctx* h = new (std::nothrow) olb_ctx();
+  if (!h) return fail(OLB_ENOMEM, "host allocation failed");
+  h->grid = *grid;
+  h->vs_id = velocity_set;
+  h->N = hermite_order;
+  h->p = opt.interp_order;
+  h->storage = opt.storage;
+  h->comp = opt.compressible ? 1 : 0;
+  h->allow_inexact = opt.allow_inexact;
+  h->tau = tau;
+  h->dt = dt;
+  h->gamma = opt.gamma;
+  h->mu = opt.mu;
+  h->rho0 = opt.rho0;
+  h->cs_scale = opt.cs_scale;
+  h->cs = cs;
+  h->set = vs;
+  for (int i = 0; i < vs.Q; ++i)
+    for (int a = 0; a < 3; ++a) h->set.xi[i][a] = vs.xi[i][a] * opt.cs_scale;
+  h->set.cs = cs;
+  h->Q = vs.Q;
+  h->D = vs.D;
+  h->planes = h->comp ? 2 * vs.Q : vs.Q;
+  h->elem = storage_bytes(opt.storage);
+  h->nnodes = nnodes;
+  h->stream = static_cast<cudaStream_t>(opt.stream);
+
+  if (step_info(h->D, h->p, h->storage, h->comp, &h->info) != 0) {
+    release(h);
+    return fail(OLB_EUNSUPPORTED, "interpolation order not built for this storage");
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    release(h);
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  if (h->info.ctas_per_sm < 1) {
+    release(h);
+    return fail(OLB_ECUDA, "step kernel cannot be resident on this device");
+  }
+
+  // stencil of the pull (Sec. 3, Eq. sl_streaming): delta = -xi dt / dx
+  h->m0.assign(h->Q * 3, 0);
+  h->W.assign(h->Q * 3 * (h->p + 1), 0.0);
+  for (int i = 0; i < h->Q; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double delta = -h->set.xi[i][a] * dt / grid->dx;
+      lagrange_stencil(delta, h->p, &h->m0[i * 3 + a], &h->W[(i * 3 + a) * (h->p + 1)]);
+    }
+  if (h->storage == OLB_FP64) {
+    fill_veltab<double>(h);
+    fill_stentab<double>(h);
+  } else {
+    fill_veltab<float>(h);
+    fill_stentab<float>(h);
+  }
+
+  const double Cv = 1.0 / (h->gamma - 1.0);
+  const double rho_ref = h->storage == OLB_FP64 ? 0.0 : h->rho0;
+  StepArgs& a = h->args;
+  a.nnodes = nnodes;
+  for (int k = 0; k < 3; ++k) a.n[k] = grid->n[k];
+  const int tx = 32, ty = h->D == 3 ? 8 : 64, tz = h->D == 3 ? 8 : 1;
+  a.nt[0] = (grid->n[0] + tx - 1) / tx;
+  a.nt[1] = (grid->n[1] + ty - 1) / ty;
+  a.nt[2] = (grid->n[2] + tz - 1) / tz;
+  a.ntiles = a.nt[0] * a.nt[1] * a.nt[2];
+  a.Q = h->Q;
+  a.planes = h->planes;
+  a.N = h->N;
+  const int vec = 16 / h->elem;
+  a.vec_ok = (grid->n[0] % vec) == 0;
+  a.tiny = (grid->n[0] < h->info.bxw) || (grid->n[1] < h->info.by) || (grid->n[2] < h->info.bz);
+  a.rho_ref = rho_ref;
+  a.tau = tau;
+  a.inv_tau = 1.0 / tau;
+  a.mu_dt = h->mu / (cs * cs * dt);
+  a.two_cv = 2.0 * Cv;
+  a.gfac = 2.0 * Cv - h->D;
+  a.inv_cs = 1.0 / cs;
+  a.cs2 = cs * cs;
+  a.dt = dt;
+
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    release(h);
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  long long g = (long long)sms * h->info.ctas_per_sm;
+  if (g > a.ntiles) g = a.ntiles;
+  h->step_grid = (int)g;
+  const int aux_slots = 1024;
+  h->partial_slots = h->step_grid > aux_slots ? h->step_grid : aux_slots;
+
+  const size_t cbytes = h->storage == OLB_FP64 ? 8 : 4;
+  const size_t state_bytes = (size_t)h->planes * nnodes * h->elem;
+  const size_t scratch_bytes = (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
+  for (int k = 0; k < 2; ++k) {
+    e = cudaMalloc(&h->buf[k], state_bytes);
+    if (e != cudaSuccess) {
+      release(h);
+      return fail(OLB_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
+    }
+  }
+  e = cudaMalloc(&h->scratch, scratch_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, (size_t)h->partial_slots * NRED * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_dev, NRED * sizeof(double));
+  if (e != cudaSuccess) {
+    release(h);
+    return fail(OLB_ENOMEM, "scratch buffers: " + std::string(cudaGetErrorString(e)));
+  }
+
+  AuxArgs& x = h->aux;
+  x.nnodes = nnodes;
+  x.Q = h->Q;
+  x.planes = h->planes;
+  x.D = h->D;
+  x.N = h->N;
+  x.storage = h->storage;
+  x.compressible = h->comp;
+  x.rho_ref = rho_ref;
+  x.gfac = a.gfac;
+  x.two_cv = a.two_cv;
+  x.inv_cs = a.inv_cs;
+  x.cs2 = a.cs2;
+  for (int i = 0; i < h->Q; ++i) {
+    for (int c = 0; c < 3; ++c) {
+      x.xi[i][c] = h->set.xi[i][c];
+      x.xih[i][c] = h->set.xi[i][c] / cs;
+    }
+    x.w[i] = h->set.w[i];
+    x.base[i] = rho_ref * h->set.w[i];
+    if (h->comp) x.base[h->Q + i] = rho_ref * h->set.w[i] * a.gfac;
+  }
+  x.rest_rho = h->rho0;
+  // start from the uniform rest state rho = rho0, u = 0 (theta = 1)
+  int rc0 = launch_rc(launch_init_fields(h->aux, h->buf[0], nullptr, nullptr, nullptr, h->stream), "init_rest");
+  if (rc0 != OLB_OK) {
+    release(h);
+    return rc0;
+  }
+  *out = h;
+  return OLB_OK;
+}
+
+int olb_destroy(olb_handle h) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  set_device(h);
+  cudaStreamSynchronize(h->stream);
+  release(h);
+  return OLB_OK;
+}
+
+int olb_shape(olb_handle h, int* Q, int* planes, size_t* nodes, int* dim, int* elem_bytes) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (Q) *Q = h->Q;
+  if (planes) *planes = h->planes;
+  if (nodes) *nodes = (size_t)h->nnodes;
+  if (dim) *dim = h->D;
+  if (elem_bytes) *elem_bytes = h->elem;
+  return OLB_OK;
+}
+
+int olb_stencil(olb_handle h, int* m0, double* W) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (m0) std::memcpy(m0, h->m0.data(), h->m0.size() * sizeof(int));
+  if (W) std::memcpy(W, h->W.data(), h->W.size() * sizeof(double));
+  return OLB_OK;
+}
+
+int olb_init_fields(olb_handle h, const double* rho, const double* u, const double* theta, int on_device) {
+  if (!h || !rho || !u) return fail(OLB_EINVAL, "null handle or field");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->nnodes;
+  const double *dr = rho, *du = u, *dth = theta;
+  void* tmp = nullptr;
+  if (!on_device) {
+    const size_t bytes = n * (size_t)(1 + h->D + (theta ? 1 : 0)) * sizeof(double);
+    rc = dev_alloc(h, &tmp, bytes);
+    if (rc) return rc;
+    double* t = static_cast<double*>(tmp);
+    cudaMemcpyAsync(t, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(t + n, u, n * h->D * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (theta) cudaMemcpyAsync(t + n * (1 + h->D), theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    dr = t;
+    du = t + n;
+    dth = theta ? t + n * (1 + h->D) : nullptr;
+  }
+  rc = launch_rc(launch_init_fields(h->aux, h->buf[h->cur], dr, du, dth, h->stream), "init_fields");
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    if (rc == OLB_OK) rc = stream_sync(h, 0);
+  }
+  h->have_partials = 0;
+  return rc;
+}
+
+int olb_step(olb_handle h, int n) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (n < 0) return fail(OLB_EINVAL, "negative step count");
+  int rc = set_device(h);
+  if (rc) return rc;
+  StepLaunch L;
+  L.a = h->args;
+  L.D = h->D;
+  L.P = h->p;
+  L.storage = h->storage;
+  L.compressible = h->comp;
+  L.veltab = h->veltab.data();
+  L.stentab = h->stentab.data();
+  L.grid = h->step_grid;
+  L.stream = h->stream;
+  L.a.scratch = h->scratch;
+  L.a.partials = h->partials;
+  for (int s = 0; s < n; ++s) {
+    L.a.src = h->buf[h->cur];
+    L.a.dst = h->buf[h->cur ^ 1];
+    int r;
+    switch (h->storage) {
+      case OLB_FP64: r = launch_step_f64(L); break;
+      case OLB_FP32_SHIFTED: r = launch_step_f32(L); break;
+      case OLB_BF16_SHIFTED: r = launch_step_bf16(L); break;
+      default: r = launch_step_f16(L); break;
+    }
+    rc = launch_rc(r, "sl_step");
+    if (rc) return rc;
+    h->cur ^= 1;
+    h->partials_from_step = 1;
+    h->have_partials = 1;
+  }
+  return OLB_OK;
+}
+
+int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_device) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->nnodes;
+  double *dr = rho, *du = u, *dth = theta;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, n * (size_t)(2 + h->D) * sizeof(double));
+    if (rc) return rc;
+    double* t = static_cast<double*>(tmp);
+    dr = rho ? t : nullptr;
+    du = u ? t + n : nullptr;
+    dth = theta ? t + n * (1 + h->D) : nullptr;
+  }
+  rc = launch_rc(launch_state_moments(h->aux, h->buf[h->cur], dr, du, dth, nullptr, 1024, h->stream),
+                 "state_moments");
+  if (rc == OLB_OK && !on_device) {
+    double* t = static_cast<double*>(tmp);
+    if (rho) cudaMemcpyAsync(rho, t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (u) cudaMemcpyAsync(u, t + n, n * h->D * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (theta) cudaMemcpyAsync(theta, t + n * (1 + h->D), n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    int r2 = stream_sync(h, 0);
+    if (rc == OLB_OK) rc = r2;
+  }
+  return rc;
+}
+
+int olb_reductions(olb_handle h, double out[8]) {
+  if (!h || !out) return fail(OLB_EINVAL, "null handle or output");
+  int rc = set_device(h);
+  if (rc) return rc;
+  int slots;
+  const bool from_step = h->have_partials && h->partials_from_step;
+  if (from_step) {
+    slots = h->step_grid;
+  } else {
+    slots = 1024;
+    rc = launch_rc(launch_state_moments(h->aux, h->buf[h->cur], nullptr, nullptr, nullptr, h->partials, slots,
+                                        h->stream),
+                   "state_moments");
+    if (rc) return rc;
+  }
+  rc = launch_rc(launch_reduce_final(h->partials, slots, h->red_dev, h->stream), "reduce_final");
+  if (rc) return rc;
+  rc = copy_out(h, out, h->red_dev, NRED * sizeof(double), 0);
+  if (rc) return rc;
+  const double nn = (double)h->nnodes;
+  out[0] /= nn;
+  out[1] /= nn;
+  out[2] = from_step ? out[2] / nn : NAN;
+  if (out[7] > 0.0) return fail(OLB_ENONFINITE, "state holds non-finite values");
+  return OLB_OK;
+}
+
+int olb_kinetic_energy(olb_handle h, double* k, double* dissipation) {
+  double r[NRED];
+  int rc = olb_reductions(h, r);
+  if (k) *k = r[0];
+  if (dissipation) *dissipation = r[2];
+  return rc;
+}
+
+int olb_get_populations(olb_handle h, double* f, int on_device) {
+  if (!h || !f) return fail(OLB_EINVAL, "null handle or buffer");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->planes * h->nnodes * sizeof(double);
+  double* d = f;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, bytes);
+    if (rc) return rc;
+    d = static_cast<double*>(tmp);
+  }
+  rc = launch_rc(launch_to_f64(h->aux, h->buf[h->cur], d, h->stream), "to_f64");
+  if (rc == OLB_OK && !on_device) rc = copy_out(h, f, d, bytes, 0);
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    int r2 = stream_sync(h, 0);
+    if (rc == OLB_OK) rc = r2;
+  }
+  return rc;
+}
+
+int olb_set_populations(olb_handle h, const double* f, int on_device) {
+  if (!h || !f) return fail(OLB_EINVAL, "null handle or buffer");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->planes * h->nnodes * sizeof(double);
+  const double* d = f;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync");
+    d = static_cast<const double*>(tmp);
+  }
+  if (rc == OLB_OK) rc = launch_rc(launch_from_f64(h->aux, h->buf[h->cur], d, h->stream), "from_f64");
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    int r2 = stream_sync(h, 0);
+    if (rc == OLB_OK) rc = r2;
+  }
+  h->have_partials = 0;
+  return rc;
+}
+
+size_t olb_state_bytes(olb_handle h) {
+  if (!h) return 0;
+  return (size_t)h->planes * h->nnodes * h->elem;
+}
+
+int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device) {
+  if (!h || !buf) return fail(OLB_EINVAL, "null handle or buffer");
+  if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
+  int rc = set_device(h);
+  if (rc) return rc;
+  return copy_out(h, buf, h->buf[h->cur], bytes, on_device);
+}
+
+int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
+  if (!h || !buf) return fail(OLB_EINVAL, "null handle or buffer");
+  if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
+  int rc = set_device(h);
+  if (rc) return rc;
+  h->have_partials = 0;
+  return copy_in(h, h->buf[h->cur], buf, bytes, on_device);
+}
+
+int olb_synchronize(olb_handle h, int timeout_ms) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  int rc = set_device(h);
+  if (rc) return rc;
+  return stream_sync(h, timeout_ms);
+}
+
+const char* olb_strerror(int code) {
+  switch (code) {
+    case OLB_OK: return "ok";
+    case OLB_EINVAL: return "invalid argument";
+    case OLB_ENOMEM: return "out of memory";
+    case OLB_ECUDA: return "CUDA runtime error";
+    case OLB_ENONFINITE: return "non-finite values in the state";
+    case OLB_ETIMEOUT: return "timed out";
+    case OLB_EBOUNDS: return "size out of bounds";
+    case OLB_EUNSUPPORTED: return "unsupported configuration";
+    case OLB_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* olb_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

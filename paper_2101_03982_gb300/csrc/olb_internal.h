@@ -1,0 +1,116 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace olb {
+
+constexpr int MAXQ = 45;       // largest velocity set (D3Q45)
+constexpr int MAXPLANES = 90;  // f and g planes of D3Q45
+constexpr int MAXP = 6;        // largest interpolation degree built
+constexpr int NRED = 8;        // global reductions per step
+
+struct VelocitySet {
+  int Q, D, degree;
+  double cs;
+  double xi[MAXQ][3];
+  double w[MAXQ];
+};
+
+// Fill *vs with the unscaled table of set `id` (olb_velocity_set); -1 if unknown.
+int velocity_set(int id, VelocitySet* vs);
+
+// Per-velocity tables in the arithmetic type C of the step (kernel parameter).
+template <typename C>
+struct VelTab {
+  C xi[MAXQ][3];   // abscissae (scaled)
+  C xih[MAXQ][3];  // xi / c_s
+  C w[MAXQ];
+  C xi2[MAXQ];     // |xi|^2
+  C rD[MAXQ];      // |xi/c_s|^2 - D
+  C rpoly[MAXQ];   // r^2 - 2 (D+2) r + D (D+2), r = |xi/c_s|^2
+  C xx[MAXQ][6];   // xi_a xi_b: xx, yy, zz, xy, xz, yz (2D: xx, yy, 0, xy, 0, 0)
+};
+
+// Fixed separable stencil of the pull: first support point and Lagrange
+// weights per velocity and axis; bit a of active[i] set when xi_{i,a} != 0.
+template <typename C, int P1>
+struct StencilTab {
+  int m0[MAXQ][3];
+  int active[MAXQ];
+  C W[MAXQ][3][P1];
+};
+
+// Scalars of one step launch.
+struct StepArgs {
+  const void* src;      // planes of the current state
+  void* dst;            // planes of the next state
+  void* scratch;        // per-CTA staging of pulled populations
+  double* partials;     // per-CTA reduction partials [grid][NRED]
+  long long nnodes;     // plane stride (elements)
+  int n[3];             // grid size (n[2] = 1 in 2D)
+  int nt[3];            // tiles per axis
+  int ntiles;
+  int Q, planes, N;
+  int vec_ok;           // 16-byte aligned rows: async vector loads
+  int tiny;             // box wider than the grid along some axis: modulo wrap
+  double rho_ref;       // rho0 for shifted storage, 0 for FP64
+  double inv_tau;       // isothermal 1/tau
+  double tau;           // isothermal tau
+  double mu_dt;         // compressible: mu / (c_s^2 dt)
+  double two_cv;        // 2 C_v
+  double gfac;          // 2 C_v - D
+  double inv_cs;        // 1 / c_s
+  double cs2;           // c_s^2
+  double dt;
+};
+
+// Launch of the fused step for storage `storage` (olb_storage); returns a
+// cudaError_t value (0 on success) or -1 when the combination is not built.
+struct StepLaunch {
+  StepArgs a;
+  int D, P, storage, compressible;
+  const void* veltab;   // VelTab<C>
+  const void* stentab;  // StencilTab<C, P+1>
+  int grid;             // CTAs
+  void* stream;
+};
+
+int launch_step_f64(const StepLaunch& L);
+int launch_step_f32(const StepLaunch& L);
+int launch_step_bf16(const StepLaunch& L);
+int launch_step_f16(const StepLaunch& L);
+
+// Shape and occupancy of the step kernel of a configuration: resident CTAs
+// per SM, dynamic shared memory, staged box extents and nodes per tile.
+struct StepInfo {
+  int ctas_per_sm;
+  size_t smem;
+  int bxw, by, bz, tile;
+};
+int step_info_f64(int D, int P, int comp, StepInfo* out);
+int step_info_f32(int D, int P, int comp, StepInfo* out);
+int step_info_bf16(int D, int P, int comp, StepInfo* out);
+int step_info_f16(int D, int P, int comp, StepInfo* out);
+
+// Auxiliary kernels (olb_aux.cu).
+struct AuxArgs {
+  long long nnodes;
+  int Q, planes, D, N, storage, compressible;
+  double rho_ref, gfac, two_cv, inv_cs, cs2;
+  double rest_rho;          // init without fields: rho = rest_rho, u = 0, theta = 1
+  double base[MAXPLANES];   // shift per plane (0 for FP64)
+  double xi[MAXQ][3];
+  double xih[MAXQ][3];
+  double w[MAXQ];
+};
+int launch_init_fields(const AuxArgs& a, void* state, const double* rho, const double* u,
+                       const double* theta, void* stream);
+int launch_state_moments(const AuxArgs& a, const void* state, double* rho, double* u,
+                         double* theta, double* partials, int grid, void* stream);
+int launch_to_f64(const AuxArgs& a, const void* state, double* f, void* stream);
+int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream);
+int launch_reduce_final(const double* partials, int nslots, double* out, void* stream);
+
+}  // namespace olb
