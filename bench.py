@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Throughput of the fused semi-Lagrangian LB step on GB300 (one JSON line).
+
+Default workload (N = 1): 3D Taylor-Green vortex, Re = 1600, Ma = 0.1, 128^3
+periodic nodes, D3Q27, N = 2 Hermite equilibrium, p = 4 Lagrange pull,
+Courant 0.4, FP32 shifted storage.  One step = one launch of the fused kernel
+over every node.  The L2 cache is flushed (a 256 MiB write) between timed
+steps, and each step is timed alone with CUDA events on the simulation's
+stream.  Under torchrun (N > 1) every rank runs its own replica of the
+workload (weak scaling, no data-path collective); rank 0 reports the whole-job
+node updates per second over the slowest rank.
+
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same
+workload (host cores only); it is the deliberately slow correctness
+reference, not a tuned CPU solver.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (million node updates per second of the semi-Lagrangian LB step)"
+WORKLOAD = dict(velocity_set="D3Q27", n=128, Re=1600.0, Ma=0.1, courant=0.4, N=2, p=4, storage="fp32",
+                log_every=10)
+FALLBACK_HBM_GBS = 6800.0
+# DRAM traffic (read + write bytes per launch) of the step kernel for the
+# default workload, from one ncu capture of the kernel source with this hash
+# (summary in profiles/); reported as null once the kernel source changes.
+TRAFFIC = {"kernel_sha": None, "bytes": None}
+
+
+def workload_name(w):
+    return (f"3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
+            f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
+            f"{w['storage'].upper()} {'shifted ' if w['storage'] != 'fp64' else ''}storage, "
+            f"k and dissipation every {w.get('log_every', 1)} steps")
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("olb_step.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_2101_03982_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+    return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 measurement)"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 3 + k and r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU measurements
+# ---------------------------------------------------------------------------
+def make_sim(w, torch):
+    from paper_2101_03982_gb300 import inputs, olb, params
+    if w.get("compressible"):
+        if w["velocity_set"].startswith("D2"):
+            rp = None
+            nx, ny = w["shape"]
+            _, _, cs, mx, _ = olb.velocity_set_info(w["velocity_set"])
+            dt = w["courant"] * 1.0 / mx
+            mu = math.sqrt(1.4) * w["Ma"] * (0.075 * ny) / w["Re"]
+            sim = olb.Sim((nx, ny), 1.0, w["velocity_set"], w["N"], 1.0, dt, interp_order=w["p"],
+                          storage=w["storage"], compressible=True, gamma=1.4, mu=mu,
+                          log_every=w.get("log_every", 10))
+            rho, u, th = inputs.shock_vortex(nx, ny)
+            sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda(),
+                            torch.from_numpy(th).cuda())
+            return sim, int(nx * ny)
+        rp = params.tgv_compressible(w["velocity_set"], w["n"], w["Re"], w["Ma"], w["courant"])
+        sim = olb.Sim((w["n"],) * 3, rp.dx, w["velocity_set"], w["N"], rp.tau, rp.dt, interp_order=w["p"],
+                      storage=w["storage"], compressible=True, gamma=rp.gamma, mu=rp.mu,
+                      log_every=w.get("log_every", 10))
+        rho, u, th = inputs.ctic3d(w["n"], rp.u0)
+        sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(th).cuda())
+        return sim, w["n"] ** 3
+    if w["velocity_set"] == "D2Q9":
+        rp = params.tgv2d_lattice(w["n"])
+        sim = olb.Sim((w["n"],) * 2, rp.dx, "D2Q9", w["N"], rp.tau, rp.dt, interp_order=w["p"],
+                      storage=w["storage"], cs_scale=rp.cs_scale, log_every=w.get("log_every", 10))
+        rho, u = inputs.tgv2d(w["n"], rp.u0, rp.cs ** 2)
+        sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        return sim, w["n"] ** 2
+    rp = params.tgv_isothermal(w["velocity_set"], w["n"], w["Re"], w["Ma"], w["courant"])
+    sim = olb.Sim((w["n"],) * 3, rp.dx, w["velocity_set"], w["N"], rp.tau, rp.dt, interp_order=w["p"],
+                  storage=w["storage"], cs_scale=rp.cs_scale, log_every=w.get("log_every", 10))
+    rho, u = inputs.tgv3d(w["n"], rp.u0, rp.cs ** 2)
+    sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    return sim, w["n"] ** 3
+
+
+def time_steps(sim, torch, steps, warmup, flush):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s, e in ev:
+        flush.zero_()
+        s.record(stream)
+        sim.step(1)
+        e.record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) * 1e-3 for s, e in ev]
+
+
+def per_set_table(torch, flush):
+    """Secondary lines: other sets, precisions and the other configurations."""
+    rows = []
+    specs = []
+    for vs in ("D3Q13", "D3Q21", "D3V27", "D3Q27"):
+        for st in ("fp32", "bf16", "fp64"):
+            specs.append(dict(WORKLOAD, velocity_set=vs, storage=st))
+    specs.append(dict(WORKLOAD, velocity_set="D3V27", N=3))
+    specs.append(dict(WORKLOAD, velocity_set="D3Q45", N=2))
+    specs.append(dict(WORKLOAD, n=256))
+    specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
+    specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0))
+    specs.append(dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
+                      Ma=1.2, Re=800.0, courant=0.4))
+    specs.append(dict(velocity_set="D2Q25", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
+                      Ma=1.2, Re=800.0, courant=0.4))
+    specs.append(dict(velocity_set="D2Q9", n=64, N=2, p=3, storage="fp64", courant=0.4, Re=100.0, Ma=0.0866))
+    hbm, _ = measured_peaks()
+    for w in specs:
+        try:
+            sim, nodes = make_sim(w, torch)
+        except Exception as e:  # a configuration that does not fit or is not built
+            rows.append(dict(config=w, error=str(e)))
+            continue
+        steps = 5 if w["storage"] == "fp64" else 10
+        ts = time_steps(sim, torch, steps, 2, flush)
+        t = statistics.mean(ts)
+        s = sim.elem_bytes
+        nbytes = 2 * sim.planes * s * nodes
+        rows.append(dict(velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
+                         N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
+                         mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
+                         gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    return rows
+
+
+def e2e_measure(w, torch, steps=8):
+    """Through the C ABI with host buffers: upload the state from pinned host
+    memory, one step, read back the kinetic energy (device -> host)."""
+    sim, nodes = make_sim(w, torch)
+    nb = sim.state_bytes()
+    host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    sim.get_state(host.numpy())
+    for _ in range(2):
+        sim.set_state(host.numpy())
+        sim.step(1)
+        sim.kinetic_energy()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_state(host.numpy())
+        sim.step(1)
+        sim.kinetic_energy()
+    dt = (time.perf_counter() - t0) / steps
+    sim.close()
+    return dict(value=round(nodes / dt / 1e6, 2), unit="MLUPS", h2d_bytes_per_step=int(nb),
+                d2h_bytes_per_step=64, steps=steps)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on bounded samples
+# ---------------------------------------------------------------------------
+def oracle_setup(w):
+    from oracle import sllbm as O
+    from oracle import velocity_sets as V
+    from paper_2101_03982_gb300 import inputs
+    vs0 = V.get(w["velocity_set"])
+    cs = 1.0 / w["Ma"]
+    vs = vs0.scaled(cs / vs0.cs)
+    n = w["n"]
+    dx = 2 * math.pi / n
+    dt = w["courant"] * dx / np.abs(vs.xi).max()
+    tau = O.tau_isothermal(1.0 / w["Re"], vs.cs, dt)
+    prm = O.Params(vs, w["N"], w["p"], dt=dt, dx=dx, tau=tau)
+    rho, u = inputs.tgv3d(n, 1.0, vs.cs ** 2)
+    f, _ = O.init_equilibrium(prm, rho, u)
+    return prm, f
+
+
+def oracle_time(prm, f, npts, seed):
+    from oracle import sllbm as O
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, f.shape[1], (npts, 3))
+    t0 = time.perf_counter()
+    O.step_at_points(prm, f, None, pts)
+    return time.perf_counter() - t0
+
+
+def calibrate(prm, f, seconds):
+    t = oracle_time(prm, f, 512, 0)
+    return max(256, int(512 * seconds / max(t, 1e-6)))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = WORKLOAD
+    prm, f = oracle_setup(w)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    npts = min(200000, calibrate(prm, f, budget))
+    for k in range(args.warmup):
+        oracle_time(prm, f, npts, 100 + k)
+    ts = [oracle_time(prm, f, npts, 1000 + k) for k in range(args.steps)]
+    t = statistics.mean(ts)
+    v = npts / t / 1e6
+    sample = f"{npts} random nodes of the {w['n']}^3 workload per step (oracle step_at_points)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "nodes_per_step": npts},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-per-set", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2101_03982_gb300 import olb
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    olb.lib()
+    args.warmup = max(3, args.warmup)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    w = WORKLOAD
+    sim, nodes = make_sim(w, torch)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ts = time_steps(sim, torch, args.steps, 0, flush)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = statistics.mean(ts)
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    k, eps = sim.kinetic_energy()
+    s = sim.elem_bytes
+    bytes_per_launch = 2 * sim.planes * s * nodes
+    hbm, peak_src = measured_peaks()
+    achieved = bytes_per_launch / t / 1e9
+    sha = kernel_sha()
+    traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_sha"] == sha else None
+    sim.close()
+    del sim
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    e2e = e2e_measure(w, torch)
+    per_set = [] if args.no_per_set else per_set_table(torch, flush)
+    cpu = None
+    if not args.no_cpu:
+        prm, f = oracle_setup(w)
+        npts = min(200000, calibrate(prm, f, 12.0))
+        tc = oracle_time(prm, f, npts, 7)
+        cpu = {"value": npts / tc / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{npts} random nodes of the {w['n']}^3 workload, one step (oracle step_at_points, "
+                         f"{tc:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": world * nodes / t / 1e6, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w["storage"] != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(w), "nodes": nodes, "velocity_set": w["velocity_set"],
+                   "storage": w["storage"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MiB write) between timed steps; each step timed alone"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "kernel": "sl_step_kernel (fused pull + collide)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "k_final": k,
+        "per_set": per_set,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

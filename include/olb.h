@@ -92,13 +92,14 @@ typedef struct {
   double mu;         /* dynamic viscosity (compressible; the tau argument is then ignored) */
   double rho0;       /* reference density of the shifted storage (default 1) */
   int allow_inexact; /* 1: accept a quadrature degree below 2N */
+  int log_every;     /* the global sums are accumulated on steps whose count is a multiple of this (>= 1) */
   void* stream;      /* cudaStream_t for every call of the handle; NULL = default stream */
 } olb_options;
 
 typedef struct olb_ctx* olb_handle;
 
 /* Fill *opt with defaults: p = 3, FP64, cs_scale = 1, isothermal, gamma = 1.4,
- * mu = 0, rho0 = 1, allow_inexact = 0, stream = NULL. */
+ * mu = 0, rho0 = 1, allow_inexact = 0, log_every = 1, stream = NULL. */
 void olb_default_options(olb_options* opt);
 
 /* Abscissae count Q, dimension D, c_s, largest |xi_{i,alpha}| and degree of a
@@ -133,15 +134,18 @@ int olb_init_fields(olb_handle h, const double* rho, const double* u, const doub
                     int on_device);
 
 /* Advance n >= 0 steps (pull, then collide).  Asynchronous on the handle's
- * stream.  Each step also leaves per-CTA FP64 partial sums of the global
- * reductions, which olb_reductions() combines. */
+ * stream.  A step whose running count (since olb_create) is a multiple of
+ * log_every also leaves per-CTA FP64 partial sums of the global reductions,
+ * which olb_reductions() combines.  Device memory: the handle keeps each
+ * plane with ghost layers of periodic copies around the interior, which the
+ * step refreshes as it writes. */
 int olb_step(olb_handle h, int n);
 
 /* rho [n], u [D][n], theta [n] (nullable) of the stored post-collision state. */
 int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_device);
 
-/* Global sums of the most recent step (or of the stored state when no step
- * has run since it was set), in a fixed summation order:
+/* Global sums of the most recent step when that step accumulated them (else
+ * of the stored state, with eps = NaN), in a fixed summation order:
  *   out[0] k     = mean |u|^2/2                       (Sec. 4.2, kinetic energy)
  *   out[1] k_rho = mean rho |u|^2/2
  *   out[2] eps   = mean 2 nu S:S, S = -Pi_neq/(2 P tau dt) (estimator; NaN without a step)
@@ -149,7 +153,8 @@ int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_devi
  *   out[4..6]    = sum rho u (x, y, z)
  *   out[7]       = number of nodes with non-finite rho, u or theta
  * Synchronises the stream.  Returns OLB_ENONFINITE (after filling out) when
- * out[7] > 0. */
+ * out[7] > 0, and OLB_ETIMEOUT when a step kernel gave up waiting for one of
+ * its staging copies (bounded wait; the step's output is then invalid). */
 int olb_reductions(olb_handle h, double out[8]);
 
 /* k and (nullable) the dissipation estimate; a view of olb_reductions(). */
@@ -159,7 +164,9 @@ int olb_kinetic_energy(olb_handle h, double* k, double* dissipation);
 int olb_get_populations(olb_handle h, double* f, int on_device);
 int olb_set_populations(olb_handle h, const double* f, int on_device);
 
-/* Raw stored state (checkpoint): exactly olb_state_bytes() bytes. */
+/* Raw stored state (checkpoint): exactly olb_state_bytes() bytes, the
+ * storage values (shifted where the storage is) as [planes][nz][ny][nx]
+ * without ghost layers.  olb_set_state also refreshes the ghost layers. */
 size_t olb_state_bytes(olb_handle h);
 int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device);
 int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);

@@ -1,7 +1,9 @@
 // Auxiliary kernels around the fused step: equilibrium initialisation from
 // macroscopic fields (Sec. 3 equilibrium with Appendix A moments), moments of
-// a stored state, FP64 <-> storage conversion, and the fixed-order final sum
-// of the per-CTA reduction partials.  None of them is on the per-step path.
+// a stored state, FP64 <-> storage conversion, compact <-> padded copies, and
+// the fixed-order final sum of the per-CTA reduction partials.  None of them
+// is on the per-step path.  Every writer also fills the periodic copies in the
+// ghost layers.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -32,6 +34,13 @@ __device__ __forceinline__ double to_double(S v) { return (double)Store<S>::ld(v
 
 constexpr int AUX_NT = 256;
 
+__device__ __forceinline__ void node_xyz(const Padded& P, long long node, int& x, int& y, int& z) {
+  x = (int)(node % P.n[0]);
+  const long long r = node / P.n[0];
+  y = (int)(r % P.n[1]);
+  z = (int)(r / P.n[1]);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(AUX_NT) init_kernel(const __grid_constant__ AuxArgs a, S* state, const double* rho,
                                                    const double* u, const double* theta) {
@@ -39,6 +48,8 @@ __global__ void __launch_bounds__(AUX_NT) init_kernel(const __grid_constant__ Au
   const bool comp = a.compressible != 0;
   for (long long node = blockIdx.x * (long long)AUX_NT + threadIdx.x; node < n;
        node += (long long)gridDim.x * AUX_NT) {
+    int x, y, z;
+    node_xyz(a.pad, node, x, y, z);
     const double r = rho ? rho[node] : a.rest_rho;
     const double ux = rho ? u[node] : 0.0, uy = rho ? u[n + node] : 0.0;
     const double uz = (rho && a.D == 3) ? u[2 * n + node] : 0.0;
@@ -53,8 +64,10 @@ __global__ void __launch_bounds__(AUX_NT) init_kernel(const __grid_constant__ Au
       const double rD = xr - a.D, rp = xr * xr - 2.0 * (a.D + 2) * xr + a.D * (a.D + 2.0);
       const double s = a.xih[i][0] * uhx + a.xih[i][1] * uhy + a.xih[i][2] * uhz;
       const double ph = comp ? phi_m1<double, true>(s, q, t, rD, rp, a.N) : phi_m1<double, false>(s, q, t, rD, rp, a.N);
-      state[(long long)i * n + node] = from_double<S>(a.w[i] * (A + r * ph));
-      if (comp) state[(long long)(a.Q + i) * n + node] = from_double<S>(a.w[i] * a.gfac * (gA + rth * ph));
+      store_all_images(state + (long long)i * a.pad.plane, a.pad, x, y, z, from_double<S>(a.w[i] * (A + r * ph)));
+      if (comp)
+        store_all_images(state + (long long)(a.Q + i) * a.pad.plane, a.pad, x, y, z,
+                         from_double<S>(a.w[i] * a.gfac * (gA + rth * ph)));
     }
   }
 }
@@ -68,15 +81,18 @@ __global__ void __launch_bounds__(AUX_NT) moments_kernel(const __grid_constant__
   for (int q = 0; q < NRED; ++q) red[q] = 0.0;
   for (long long node = blockIdx.x * (long long)AUX_NT + threadIdx.x; node < n;
        node += (long long)gridDim.x * AUX_NT) {
+    int x, y, z;
+    node_xyz(a.pad, node, x, y, z);
+    const long long off = pad_index(a.pad, x, y, z);
     double A = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, B = 0.0, G = 0.0;
     for (int i = 0; i < a.Q; ++i) {
-      const double v = to_double(state[(long long)i * n + node]);
+      const double v = to_double(state[(long long)i * a.pad.plane + off]);
       A += v;
       jx += a.xi[i][0] * v;
       jy += a.xi[i][1] * v;
       jz += a.xi[i][2] * v;
       B += (a.xi[i][0] * a.xi[i][0] + a.xi[i][1] * a.xi[i][1] + a.xi[i][2] * a.xi[i][2]) * v;
-      if (comp) G += to_double(state[(long long)(a.Q + i) * n + node]);
+      if (comp) G += to_double(state[(long long)(a.Q + i) * a.pad.plane + off]);
     }
     const double r = a.rho_ref + A;
     const double ux = jx / r, uy = jy / r, uz = jz / r;
@@ -92,7 +108,7 @@ __global__ void __launch_bounds__(AUX_NT) moments_kernel(const __grid_constant__
     if (theta) theta[node] = th;
     red[0] += 0.5 * u2;
     red[1] += 0.5 * r * u2;
-    red[3] += r;
+    red[3] += A;
     red[4] += jx;
     red[5] += jy;
     red[6] += jz;
@@ -114,12 +130,15 @@ __global__ void __launch_bounds__(AUX_NT) moments_kernel(const __grid_constant__
   }
 }
 
+// compact element e = plane * nnodes + node
 template <typename S>
 __global__ void to_f64_kernel(const __grid_constant__ AuxArgs a, const S* state, double* f) {
   const long long total = (long long)a.planes * a.nnodes;
   for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
     const int p = (int)(e / a.nnodes);
-    f[e] = to_double(state[e]) + a.base[p];
+    int x, y, z;
+    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
+    f[e] = to_double(state[(long long)p * a.pad.plane + pad_index(a.pad, x, y, z)]) + a.base[p];
   }
 }
 
@@ -128,7 +147,31 @@ __global__ void from_f64_kernel(const __grid_constant__ AuxArgs a, S* state, con
   const long long total = (long long)a.planes * a.nnodes;
   for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
     const int p = (int)(e / a.nnodes);
-    state[e] = from_double<S>(f[e] - a.base[p]);
+    int x, y, z;
+    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
+    store_all_images(state + (long long)p * a.pad.plane, a.pad, x, y, z, from_double<S>(f[e] - a.base[p]));
+  }
+}
+
+template <typename S>
+__global__ void gather_kernel(const __grid_constant__ AuxArgs a, const S* state, S* compact) {
+  const long long total = (long long)a.planes * a.nnodes;
+  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
+    const int p = (int)(e / a.nnodes);
+    int x, y, z;
+    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
+    compact[e] = state[(long long)p * a.pad.plane + pad_index(a.pad, x, y, z)];
+  }
+}
+
+template <typename S>
+__global__ void scatter_kernel(const __grid_constant__ AuxArgs a, S* state, const S* compact) {
+  const long long total = (long long)a.planes * a.nnodes;
+  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
+    const int p = (int)(e / a.nnodes);
+    int x, y, z;
+    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
+    store_all_images(state + (long long)p * a.pad.plane, a.pad, x, y, z, compact[e]);
   }
 }
 
@@ -150,7 +193,7 @@ __global__ void __launch_bounds__(256) reduce_final_kernel(const double* partial
 
 int aux_grid(long long work) {
   long long g = (work + AUX_NT - 1) / AUX_NT;
-  if (g > 4096) g = 4096;
+  if (g > 8192) g = 8192;
   if (g < 1) g = 1;
   return (int)g;
 }
@@ -198,6 +241,24 @@ int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     from_f64_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, f);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    gather_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state,
+                                                                                                    (S*)compact);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    scatter_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state,
+                                                                                                     (const S*)compact);
     return (int)cudaGetLastError();
   });
 }

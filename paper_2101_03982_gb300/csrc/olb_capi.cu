@@ -1,7 +1,10 @@
 // C ABI of the library (include/olb.h): handle lifetime, argument checks,
 // stencil and table set-up on the host, and dispatch of the kernels.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -43,9 +46,13 @@ struct olb_ctx {
   void* scratch = nullptr;
   double* partials = nullptr;
   double* red_dev = nullptr;
+  int* err_dev = nullptr;
   int step_grid = 0, partial_slots = 0;
-  int partials_from_step = 0;  // 1: the partials hold the last step's sums
-  int have_partials = 0;
+  int log_every = 1;
+  long long step_count = 0;
+  int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
+  Padded pad{};
+  TmaMaps maps{};
   cudaStream_t stream = nullptr;
   int device = 0;
   StepInfo info{};
@@ -155,7 +162,86 @@ void release(olb_ctx* h) {
   if (h->scratch) cudaFree(h->scratch);
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
+  if (h->err_dev) cudaFree(h->err_dev);
   delete h;
+}
+
+// Ghost widths from the stencil reach: on each axis the pull reads offsets
+// m0 .. m0 + p of every active velocity; x is widened to keep rows and staged
+// boxes on 16-byte (and 4-node) boundaries.
+void layout_padding(olb_ctx* h) {
+  Padded& P = h->pad;
+  const int align = std::max(16 / h->elem, 4);
+  for (int a = 0; a < 3; ++a) {
+    int lo = 0, hi = 0;
+    if (a < h->D)
+      for (int i = 0; i < h->Q; ++i) {
+        if (h->set.xi[i][a] == 0.0) continue;
+        lo = std::max(lo, -h->m0[i * 3 + a]);
+        hi = std::max(hi, h->m0[i * 3 + a] + h->p);
+      }
+    P.n[a] = h->grid.n[a];
+    if (a == 0) {
+      P.gl[0] = (lo + align - 1) / align * align;
+      const int np = (P.gl[0] + P.n[0] + hi + align - 1) / align * align;
+      P.gr[0] = np - P.gl[0] - P.n[0];
+    } else {
+      P.gl[a] = lo;
+      P.gr[a] = hi;
+    }
+    P.np[a] = P.gl[a] + P.n[a] + P.gr[a];
+  }
+  P.plane = (long long)P.np[0] * P.np[1] * P.np[2];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// One 4D tiled descriptor (x, y, z, plane) per buffer and staged box shape.
+int build_maps(olb_ctx* h) {
+  auto enc = encode_fn();
+  if (!enc) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled is not available");
+  CUtensorMapDataType dt;
+  switch (h->storage) {
+    case OLB_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+    case OLB_FP32_SHIFTED: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case OLB_BF16_SHIFTED: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+  }
+  const Padded& P = h->pad;
+  const cuuint64_t dims[4] = {(cuuint64_t)P.np[0], (cuuint64_t)P.np[1], (cuuint64_t)P.np[2], (cuuint64_t)h->planes};
+  const cuuint64_t strides[3] = {(cuuint64_t)P.np[0] * h->elem, (cuuint64_t)P.np[0] * P.np[1] * h->elem,
+                                 (cuuint64_t)P.plane * h->elem};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int b = 0; b < 2; ++b)
+    for (int v = 0; v < 4; ++v) {
+      const cuuint32_t box[4] = {(cuuint32_t)h->info.bxw, (cuuint32_t)((v & 1) ? h->info.by : h->info.ty),
+                                 (cuuint32_t)((v & 2) ? h->info.bz : h->info.tz), 1};
+      CUresult r = enc(&h->maps.m[b][v], dt, 4, h->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    }
+  return OLB_OK;
+}
+
+// Device error flag set by a step kernel whose bounded wait ran out.
+int check_err(olb_ctx* h) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "error flag");
+  if (v) return fail(OLB_ETIMEOUT, "a step kernel gave up waiting for a staging copy; the state is invalid");
+  return OLB_OK;
 }
 
 int set_device(olb_ctx* h) {
@@ -229,6 +315,7 @@ void olb_default_options(olb_options* opt) {
   opt->mu = 0.0;
   opt->rho0 = 1.0;
   opt->allow_inexact = 0;
+  opt->log_every = 1;
   opt->stream = nullptr;
 }
 
@@ -274,6 +361,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   if (storage_bytes(opt.storage) == 0) return fail(OLB_EINVAL, "unknown storage");
   if (!(opt.cs_scale > 0.0) || !std::isfinite(opt.cs_scale)) return fail(OLB_EINVAL, "cs_scale must be positive");
   if (!(opt.rho0 > 0.0)) return fail(OLB_EINVAL, "rho0 must be positive");
+  if (opt.log_every < 1) return fail(OLB_EINVAL, "log_every must be >= 1");
 
   VelocitySet vs;
   if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
@@ -301,6 +389,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->storage = opt.storage;
   h->comp = opt.compressible ? 1 : 0;
   h->allow_inexact = opt.allow_inexact;
+  h->log_every = opt.log_every;
   h->tau = tau;
   h->dt = dt;
   h->gamma = opt.gamma;
@@ -351,20 +440,17 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
 
   const double Cv = 1.0 / (h->gamma - 1.0);
   const double rho_ref = h->storage == OLB_FP64 ? 0.0 : h->rho0;
+  layout_padding(h);
   StepArgs& a = h->args;
-  a.nnodes = nnodes;
-  for (int k = 0; k < 3; ++k) a.n[k] = grid->n[k];
-  const int tx = 32, ty = h->D == 3 ? 8 : 64, tz = h->D == 3 ? 8 : 1;
-  a.nt[0] = (grid->n[0] + tx - 1) / tx;
-  a.nt[1] = (grid->n[1] + ty - 1) / ty;
-  a.nt[2] = (grid->n[2] + tz - 1) / tz;
+  a.pad = h->pad;
+  a.nt[0] = (grid->n[0] + h->info.tx - 1) / h->info.tx;
+  a.nt[1] = (grid->n[1] + h->info.ty - 1) / h->info.ty;
+  a.nt[2] = (grid->n[2] + h->info.tz - 1) / h->info.tz;
   a.ntiles = a.nt[0] * a.nt[1] * a.nt[2];
   a.Q = h->Q;
   a.planes = h->planes;
   a.N = h->N;
-  const int vec = 16 / h->elem;
-  a.vec_ok = (grid->n[0] % vec) == 0;
-  a.tiny = (grid->n[0] < h->info.bxw) || (grid->n[1] < h->info.by) || (grid->n[2] < h->info.bz);
+  a.quad_ok = (grid->n[0] % 4) == 0;
   a.rho_ref = rho_ref;
   a.tau = tau;
   a.inv_tau = 1.0 / tau;
@@ -388,10 +474,11 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->partial_slots = h->step_grid > aux_slots ? h->step_grid : aux_slots;
 
   const size_t cbytes = h->storage == OLB_FP64 ? 8 : 4;
-  const size_t state_bytes = (size_t)h->planes * nnodes * h->elem;
+  const size_t state_bytes = (size_t)h->planes * h->pad.plane * h->elem;
   const size_t scratch_bytes = (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
   for (int k = 0; k < 2; ++k) {
     e = cudaMalloc(&h->buf[k], state_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[k], 0, state_bytes, h->stream);
     if (e != cudaSuccess) {
       release(h);
       return fail(OLB_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
@@ -400,12 +487,27 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   e = cudaMalloc(&h->scratch, scratch_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, (size_t)h->partial_slots * NRED * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->red_dev, NRED * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->err_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) {
     release(h);
     return fail(OLB_ENOMEM, "scratch buffers: " + std::string(cudaGetErrorString(e)));
   }
+  a.buf[0] = h->buf[0];
+  a.buf[1] = h->buf[1];
+  a.scratch = h->scratch;
+  a.partials = h->partials;
+  a.err = h->err_dev;
+  {
+    int rcm = build_maps(h);
+    if (rcm != OLB_OK) {
+      release(h);
+      return rcm;
+    }
+  }
 
   AuxArgs& x = h->aux;
+  x.pad = h->pad;
   x.nnodes = nnodes;
   x.Q = h->Q;
   x.planes = h->planes;
@@ -487,7 +589,7 @@ int olb_init_fields(olb_handle h, const double* rho, const double* u, const doub
     cudaFreeAsync(tmp, h->stream);
     if (rc == OLB_OK) rc = stream_sync(h, 0);
   }
-  h->have_partials = 0;
+  h->partials_valid = 0;
   return rc;
 }
 
@@ -504,13 +606,13 @@ int olb_step(olb_handle h, int n) {
   L.compressible = h->comp;
   L.veltab = h->veltab.data();
   L.stentab = h->stentab.data();
+  L.maps = &h->maps;
   L.grid = h->step_grid;
   L.stream = h->stream;
-  L.a.scratch = h->scratch;
-  L.a.partials = h->partials;
   for (int s = 0; s < n; ++s) {
-    L.a.src = h->buf[h->cur];
-    L.a.dst = h->buf[h->cur ^ 1];
+    const long long count = h->step_count + 1;
+    L.a.src = h->cur;
+    L.a.reduce = (count % h->log_every) == 0;
     int r;
     switch (h->storage) {
       case OLB_FP64: r = launch_step_f64(L); break;
@@ -521,8 +623,8 @@ int olb_step(olb_handle h, int n) {
     rc = launch_rc(r, "sl_step");
     if (rc) return rc;
     h->cur ^= 1;
-    h->partials_from_step = 1;
-    h->have_partials = 1;
+    h->step_count = count;
+    h->partials_valid = L.a.reduce;
   }
   return OLB_OK;
 }
@@ -563,7 +665,7 @@ int olb_reductions(olb_handle h, double out[8]) {
   int rc = set_device(h);
   if (rc) return rc;
   int slots;
-  const bool from_step = h->have_partials && h->partials_from_step;
+  const bool from_step = h->partials_valid != 0;
   if (from_step) {
     slots = h->step_grid;
   } else {
@@ -577,10 +679,13 @@ int olb_reductions(olb_handle h, double out[8]) {
   if (rc) return rc;
   rc = copy_out(h, out, h->red_dev, NRED * sizeof(double), 0);
   if (rc) return rc;
+  rc = check_err(h);
+  if (rc) return rc;
   const double nn = (double)h->nnodes;
   out[0] /= nn;
   out[1] /= nn;
   out[2] = from_step ? out[2] / nn : NAN;
+  out[3] += h->aux.rho_ref * nn;
   if (out[7] > 0.0) return fail(OLB_ENONFINITE, "state holds non-finite values");
   return OLB_OK;
 }
@@ -635,7 +740,7 @@ int olb_set_populations(olb_handle h, const double* f, int on_device) {
     int r2 = stream_sync(h, 0);
     if (rc == OLB_OK) rc = r2;
   }
-  h->have_partials = 0;
+  h->partials_valid = 0;
   return rc;
 }
 
@@ -649,7 +754,21 @@ int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device) {
   if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
   int rc = set_device(h);
   if (rc) return rc;
-  return copy_out(h, buf, h->buf[h->cur], bytes, on_device);
+  void* d = buf;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, bytes);
+    if (rc) return rc;
+    d = tmp;
+  }
+  rc = launch_rc(launch_gather(h->aux, h->buf[h->cur], d, h->stream), "gather");
+  if (rc == OLB_OK && !on_device) rc = copy_out(h, buf, d, bytes, 0);
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    int r2 = stream_sync(h, 0);
+    if (rc == OLB_OK) rc = r2;
+  }
+  return rc;
 }
 
 int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
@@ -657,15 +776,32 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
   if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
   int rc = set_device(h);
   if (rc) return rc;
-  h->have_partials = 0;
-  return copy_in(h, h->buf[h->cur], buf, bytes, on_device);
+  const void* d = buf;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(tmp, buf, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync");
+    d = tmp;
+  }
+  if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], d, h->stream), "scatter");
+  if (tmp) {
+    cudaFreeAsync(tmp, h->stream);
+    int r2 = stream_sync(h, 0);
+    if (rc == OLB_OK) rc = r2;
+  }
+  h->partials_valid = 0;
+  return rc;
 }
 
 int olb_synchronize(olb_handle h, int timeout_ms) {
   if (!h) return fail(OLB_EINVAL, "null handle");
   int rc = set_device(h);
   if (rc) return rc;
-  return stream_sync(h, timeout_ms);
+  rc = stream_sync(h, timeout_ms);
+  if (rc) return rc;
+  return check_err(h);
 }
 
 const char* olb_strerror(int code) {

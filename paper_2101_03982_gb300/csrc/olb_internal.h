@@ -1,6 +1,8 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -20,6 +22,28 @@ struct VelocitySet {
 
 // Fill *vs with the unscaled table of set `id` (olb_velocity_set); -1 if unknown.
 int velocity_set(int id, VelocitySet* vs);
+
+// Device layout of one population plane: the interior n[0] x n[1] x n[2]
+// nodes surrounded by ghost layers (gl on the low side, gr on the high side of
+// each axis) that hold periodic copies, so that every staged box is a plain
+// in-bounds tile.  np = gl + n + gr; np[0] keeps rows 16-byte aligned.
+struct Padded {
+  int n[3];
+  int np[3];
+  int gl[3];
+  int gr[3];
+  long long plane;  // np[0] * np[1] * np[2]
+};
+
+#if defined(__CUDACC__)
+#define OLB_HD __host__ __device__ __forceinline__
+#else
+#define OLB_HD inline
+#endif
+
+OLB_HD long long pad_index(const Padded& P, int x, int y, int z) {
+  return ((long long)(z + P.gl[2]) * P.np[1] + (y + P.gl[1])) * P.np[0] + (x + P.gl[0]);
+}
 
 // Per-velocity tables in the arithmetic type C of the step (kernel parameter).
 template <typename C>
@@ -42,19 +66,25 @@ struct StencilTab {
   C W[MAXQ][3][P1];
 };
 
+// TMA descriptors of the two population buffers, one per staged box shape
+// (bit 0: y extended by the stencil, bit 1: z extended).
+struct TmaMaps {
+  CUtensorMap m[2][4];
+};
+
 // Scalars of one step launch.
 struct StepArgs {
-  const void* src;      // planes of the current state
-  void* dst;            // planes of the next state
+  void* buf[2];         // population buffers (padded planes)
+  int src;              // index of the current state in buf
   void* scratch;        // per-CTA staging of pulled populations
   double* partials;     // per-CTA reduction partials [grid][NRED]
-  long long nnodes;     // plane stride (elements)
-  int n[3];             // grid size (n[2] = 1 in 2D)
+  int* err;             // device error flag (1: a bounded wait ran out)
+  Padded pad;
   int nt[3];            // tiles per axis
   int ntiles;
   int Q, planes, N;
-  int vec_ok;           // 16-byte aligned rows: async vector loads
-  int tiny;             // box wider than the grid along some axis: modulo wrap
+  int reduce;           // 1: accumulate the global sums this step
+  int quad_ok;          // n[0] % 4 == 0: 4-node x groups never straddle the edge
   double rho_ref;       // rho0 for shifted storage, 0 for FP64
   double inv_tau;       // isothermal 1/tau
   double tau;           // isothermal tau
@@ -73,6 +103,7 @@ struct StepLaunch {
   int D, P, storage, compressible;
   const void* veltab;   // VelTab<C>
   const void* stentab;  // StencilTab<C, P+1>
+  const TmaMaps* maps;
   int grid;             // CTAs
   void* stream;
 };
@@ -87,7 +118,7 @@ int launch_step_f16(const StepLaunch& L);
 struct StepInfo {
   int ctas_per_sm;
   size_t smem;
-  int bxw, by, bz, tile;
+  int bxw, by, bz, tile, tx, ty, tz, vec;
 };
 int step_info_f64(int D, int P, int comp, StepInfo* out);
 int step_info_f32(int D, int P, int comp, StepInfo* out);
@@ -96,7 +127,8 @@ int step_info_f16(int D, int P, int comp, StepInfo* out);
 
 // Auxiliary kernels (olb_aux.cu).
 struct AuxArgs {
-  long long nnodes;
+  Padded pad;
+  long long nnodes;         // interior nodes
   int Q, planes, D, N, storage, compressible;
   double rho_ref, gfac, two_cv, inv_cs, cs2;
   double rest_rho;          // init without fields: rho = rest_rho, u = 0, theta = 1
@@ -111,6 +143,9 @@ int launch_state_moments(const AuxArgs& a, const void* state, double* rho, doubl
                          double* theta, double* partials, int grid, void* stream);
 int launch_to_f64(const AuxArgs& a, const void* state, double* f, void* stream);
 int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream);
+// Compact [plane][z][y][x] <-> padded state (raw storage values).
+int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream);
+int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream);
 int launch_reduce_final(const double* partials, int nslots, double* out, void* stream);
 
 }  // namespace olb

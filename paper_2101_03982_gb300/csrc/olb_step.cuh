@@ -1,20 +1,25 @@
 // Fused semi-Lagrangian pull + collide step (the hot path), sm_103a.
 //
-// One CTA owns a tile of nodes (3D: 32 x 8 x 8, 2D: 32 x 64) and walks the
-// population planes one after another.  For plane i it stages the tile plus
-// the stencil halo of velocity i in shared memory (16-byte cp.async copies,
-// double buffered so that the next plane streams in while this one is
-// interpolated), applies the separable 1D Lagrange passes z -> y -> x
-// (skipping an axis with xi_{i,alpha} = 0, where the stencil is the identity),
-// accumulates the moments of Sec. 3 in registers and parks the pulled value
-// f~_i in a per-CTA staging slab that stays in L2.  After the last plane the
-// same thread reads its own f~_i back, forms the Hermite equilibrium of
-// Appendix A in closed form, relaxes with BGK (Sec. 3) and writes the next
-// state with warp-coalesced stores.  Global sums (kinetic energy, dissipation
-// estimate, mass, momentum, non-finite count) are reduced per CTA in FP64 in a
-// fixed order.
+// Each population plane lives in HBM with ghost layers that hold periodic
+// copies of the opposite faces, so the stencil box of any tile is a plain
+// in-bounds block.  One CTA owns a tile of nodes (3D: 32 x 8 x 8, 2D: 32 x 64)
+// and walks the planes in order.  For plane i one thread issues a TMA tiled
+// copy (cp.async.bulk.tensor, completion on an mbarrier) of the tile plus the
+// stencil halo of velocity i into shared memory; the copy of plane i+1 is in
+// flight while plane i is interpolated.  The separable 1D Lagrange passes
+// z -> y -> x (Sec. 3, Eq. sl_streaming, uniform-grid form; an axis with
+// xi_{i,alpha} = 0 is the identity and is skipped) run on 4-node x groups with
+// 128-bit shared-memory accesses.  Each thread owns four consecutive x nodes:
+// it accumulates the moments of Sec. 3 and parks the pulled values f~_i in a
+// per-CTA staging slab that stays in L2.  After the last plane the thread
+// reads its f~_i back, forms the Hermite equilibrium of Appendix A in closed
+// form, relaxes with BGK (Sec. 3) and writes the new state with 128-bit stores
+// (plus the periodic copies of boundary nodes).  Optional global sums (kinetic
+// energy, dissipation estimate, mass, momentum, non-finite count) are reduced
+// per warp and tile, then per CTA in FP64 in a fixed order.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -49,13 +54,51 @@ struct Store<__half> {
   __device__ static __forceinline__ float ld(__half v) { return __half2float(v); }
   __device__ static __forceinline__ __half st(float v) { return __float2half_rn(v); }
 };
-template <typename C>
-__device__ __forceinline__ C ldc(C v) {
-  return v;
+
+// ---- four consecutive elements (one x group) -------------------------------
+__device__ __forceinline__ void ld4(const float* p, float o[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double o[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float o[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const __half* p, float o[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, const float v[4]) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<unsigned*>(&a);
+  u.y = *reinterpret_cast<unsigned*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+__device__ __forceinline__ void st4(__half* p, const float v[4]) {
+  __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<unsigned*>(&a);
+  u.y = *reinterpret_cast<unsigned*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
 }
 
-constexpr int NT = 512;  // threads per CTA
-constexpr int NPT = 4;   // nodes per thread
+constexpr int NT = 512;  // threads per CTA; each owns 4 consecutive x nodes
 
 template <int D>
 struct TileShape;
@@ -68,51 +111,135 @@ struct TileShape<2> {
   static constexpr int X = 32, Y = 64, Z = 1;
 };
 
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int roundup(int a, int m) { return (a + m - 1) / m * m; }
+
 template <int D, int P, typename S>
 struct Layout {
   using C = typename Store<S>::C;
   static constexpr int TX = TileShape<D>::X, TY = TileShape<D>::Y, TZ = TileShape<D>::Z;
   static constexpr int TILE = TX * TY * TZ;
-  static constexpr int VEC = 16 / (int)sizeof(S);
-  static constexpr int BXW = ((TX + P + VEC - 1) + VEC - 1) / VEC * VEC;
+  static constexpr int VEC = 16 / (int)sizeof(S);     // elements per 16-byte TMA granule
+  static constexpr int ALIGN = cmax(VEC, 4);          // x alignment of rows and boxes
+  static constexpr int BXW = roundup(TX + P + VEC - 1, ALIGN);
+  static constexpr int NQX = BXW / 4;                 // 4-element groups per box row
   static constexpr int BY = TY + P;
   static constexpr int BZ = D == 3 ? TZ + P : 1;
-  static constexpr int PL = BY * BXW;  // elements per z-plane of box and bufA
-  static constexpr int BOX = BZ * PL;
-  static constexpr int BUFA = D == 3 ? TZ * PL : 0;
+  static constexpr size_t BOXB = (size_t)roundup(BZ * BY * BXW * (int)sizeof(S), 128);
+  static constexpr int BUFA = D == 3 ? TZ * BY * BXW : 0;
   static constexpr int BUFB = TZ * TY * BXW;
-  static constexpr size_t BYTES =
-      2 * (size_t)BOX * sizeof(S) + (size_t)(BUFA + BUFB) * sizeof(C) + (NT / 32) * NRED * sizeof(double);
-  static_assert(TILE == NT * NPT, "tile must be NT x NPT nodes");
+  static constexpr size_t OFF_A = 2 * BOXB;
+  static constexpr size_t OFF_B = OFF_A + roundup(BUFA * (int)sizeof(C), 16);
+  static constexpr size_t OFF_R = OFF_B + roundup(BUFB * (int)sizeof(C), 16);
+  static constexpr size_t OFF_M = OFF_R + (NT / 32) * NRED * sizeof(double);
+  static constexpr size_t BYTES = OFF_M + 2 * sizeof(unsigned long long) + 128;  // +128: base alignment
+  static_assert(TILE == NT * 4, "each thread owns one 4-node x group");
+  static_assert(28 + 4 * ((VEC - 1 + 3 + P) / 4 + 1) <= BXW, "x pass reads inside the box row");
 };
 
 // ---------------------------------------------------------------------------
-// small helpers
+// mbarrier / TMA helpers (PTX)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ int wrap_mod(int x, int n) {
-  int r = x % n;
-  return r < 0 ? r + n : r;
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the copy did not land within the limit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (long spin = 0; spin < (1L << 24); ++spin)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
 }
 
-// Local node k (0..NPT-1) of this thread inside the tile.
-template <int D>
-__device__ __forceinline__ void node_of(int k, int& lx, int& ly, int& lz) {
-  const int local = threadIdx.x + NT * k;
-  lx = local & 31;
-  if (D == 3) {
-    ly = (local >> 5) & 7;
-    lz = local >> 8;
-  } else {
-    ly = local >> 5;
-    lz = 0;
-  }
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];\n" ::"l"(
+                   reinterpret_cast<unsigned long long>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
+// L2 eviction policies: the staging slab is reused within a tile (keep), the
+// new state is not read again by this launch (stream through).
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void stg16(void* p, uint4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void stg8(void* p, uint2 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;\n" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ uint4 ldg16(const void* p, unsigned long long pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+
+// Four values of the arithmetic type to / from global memory with a policy.
+__device__ __forceinline__ void gst4(float* p, const float v[4], unsigned long long pol) {
+  stg16(p, make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3])),
+        pol);
+}
+__device__ __forceinline__ void gst4(double* p, const double v[4], unsigned long long pol) {
+  const unsigned long long a = __double_as_longlong(v[0]), b = __double_as_longlong(v[1]);
+  const unsigned long long c = __double_as_longlong(v[2]), d = __double_as_longlong(v[3]);
+  stg16(p, make_uint4((unsigned)a, (unsigned)(a >> 32), (unsigned)b, (unsigned)(b >> 32)), pol);
+  stg16(p + 2, make_uint4((unsigned)c, (unsigned)(c >> 32), (unsigned)d, (unsigned)(d >> 32)), pol);
+}
+__device__ __forceinline__ void gst4(__nv_bfloat16* p, const float v[4], unsigned long long pol) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+  stg8(p, make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b)), pol);
+}
+__device__ __forceinline__ void gst4(__half* p, const float v[4], unsigned long long pol) {
+  __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+  stg8(p, make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b)), pol);
+}
+__device__ __forceinline__ void gld4(const float* p, float o[4], unsigned long long pol) {
+  const uint4 v = ldg16(p, pol);
+  o[0] = __uint_as_float(v.x); o[1] = __uint_as_float(v.y); o[2] = __uint_as_float(v.z); o[3] = __uint_as_float(v.w);
+}
+__device__ __forceinline__ void gld4(const double* p, double o[4], unsigned long long pol) {
+  const uint4 a = ldg16(p, pol), b = ldg16(p + 2, pol);
+  o[0] = __longlong_as_double(((unsigned long long)a.y << 32) | a.x);
+  o[1] = __longlong_as_double(((unsigned long long)a.w << 32) | a.z);
+  o[2] = __longlong_as_double(((unsigned long long)b.y << 32) | b.x);
+  o[3] = __longlong_as_double(((unsigned long long)b.w << 32) | b.z);
 }
 
 // Hermite series of the equilibrium (Appendix A) contracted in closed form:
@@ -141,128 +268,183 @@ __device__ __forceinline__ C phi_m1(C s, C q, C t, C rD, C rpoly, int N) {
 }
 
 // ---------------------------------------------------------------------------
-// staging of one plane's box (tile + halo) into shared memory
+// staging: one TMA copy per plane and tile
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, int BYA, int BZA>
-__device__ __forceinline__ void load_box(S* box, const S* plane, const StepArgs& a, int gx0, int gy0,
-                                         int gz0) {
-  using L = Layout<D, P, S>;
-  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
-  if (a.vec_ok) {
-    constexpr int NV = L::BXW / L::VEC;
-    constexpr int TOTAL = BZA * BYA * NV;
-    for (int e = threadIdx.x; e < TOTAL; e += NT) {
-      const int v = e % NV, r = e / NV, yy = r % BYA, zz = r / BYA;
-      int gx = gx0 + v * L::VEC, gy = gy0 + yy, gz = gz0 + zz;
-      if (a.tiny) {
-        gx %= n0; gy %= n1; gz %= n2;
-      } else {
-        gx = gx >= n0 ? gx - n0 : gx;
-        gy = gy >= n1 ? gy - n1 : gy;
-        gz = gz >= n2 ? gz - n2 : gz;
-      }
-      cp_async16(box + (zz * L::BY + yy) * L::BXW + v * L::VEC,
-                 plane + ((long long)gz * n1 + gy) * n0 + gx);
-    }
-  } else {
-    constexpr int TOTAL = BZA * BYA * L::BXW;
-    for (int e = threadIdx.x; e < TOTAL; e += NT) {
-      const int x = e % L::BXW, r = e / L::BXW, yy = r % BYA, zz = r / BYA;
-      const int gx = (gx0 + x) % n0, gy = (gy0 + yy) % n1, gz = (gz0 + zz) % n2;
-      box[(zz * L::BY + yy) * L::BXW + x] = plane[((long long)gz * n1 + gy) * n0 + gx];
-    }
-  }
-}
-
-template <int D, int P, typename S, typename VT, typename STT>
-__device__ __forceinline__ void stage_plane(S* box, const StepArgs& a, const STT& st, int plane, int tile) {
+// Origin (padded coordinates) and shape variant of the box of `plane` for `tile`.
+template <int D, int P, typename S, typename STT>
+__device__ __forceinline__ int box_origin(const StepArgs& a, const STT& st, int plane, int tile, int& X, int& Y,
+                                          int& Z) {
   using L = Layout<D, P, S>;
   const int i = plane < a.Q ? plane : plane - a.Q;
   const int tx = tile % a.nt[0], r = tile / a.nt[0];
   const int ty = r % a.nt[1], tz = r / a.nt[1];
   const int act = st.active[i];
-  const int gxs = tx * L::TX + ((act & 1) ? st.m0[i][0] : 0);
-  const int gys = ty * L::TY + ((act & 2) ? st.m0[i][1] : 0);
-  const int gzs = tz * L::TZ + ((act & 4) ? st.m0[i][2] : 0);
-  const int xa = gxs - wrap_mod(gxs, L::VEC);
-  const int gx0 = wrap_mod(xa, a.n[0]), gy0 = wrap_mod(gys, a.n[1]), gz0 = D == 3 ? wrap_mod(gzs, a.n[2]) : 0;
-  const S* src = static_cast<const S*>(a.src) + (long long)plane * a.nnodes;
-  constexpr int BY1 = L::TY + P, BY0 = L::TY;
-  constexpr int BZ1 = D == 3 ? L::TZ + P : 1, BZ0 = D == 3 ? L::TZ : 1;
-  if (act & 2) {
-    if (act & 4) load_box<D, P, S, BY1, BZ1>(box, src, a, gx0, gy0, gz0);
-    else load_box<D, P, S, BY1, BZ0>(box, src, a, gx0, gy0, gz0);
-  } else {
-    if (act & 4) load_box<D, P, S, BY0, BZ1>(box, src, a, gx0, gy0, gz0);
-    else load_box<D, P, S, BY0, BZ0>(box, src, a, gx0, gy0, gz0);
+  X = tx * L::TX + a.pad.gl[0] + ((act & 1) ? st.m0[i][0] : 0);
+  X -= X % L::VEC;
+  Y = ty * L::TY + a.pad.gl[1] + ((act & 2) ? st.m0[i][1] : 0);
+  Z = D == 3 ? tz * L::TZ + a.pad.gl[2] + ((act & 4) ? st.m0[i][2] : 0) : 0;
+  return ((act & 2) ? 1 : 0) | ((D == 3 && (act & 4)) ? 2 : 0);
+}
+
+template <int D, int P, typename S, typename STT>
+__device__ __forceinline__ void issue_box(S* dst, unsigned long long* bar, const CUtensorMap* maps4,
+                                          const StepArgs& a, const STT& st, int plane, int tile) {
+  using L = Layout<D, P, S>;
+  int X, Y, Z;
+  const int v = box_origin<D, P, S>(a, st, plane, tile, X, Y, Z);
+  const unsigned bytes = (unsigned)(L::BXW * ((v & 1) ? L::BY : L::TY) * ((v & 2) ? L::BZ : L::TZ) * sizeof(S));
+  mbar_expect_tx(bar, bytes);
+  tma_load_4d(dst, &maps4[v], X, Y, Z, plane, bar);
+}
+
+// Warm L2 with the box of a plane staged PREFETCH planes later.
+constexpr int PREFETCH = 8;
+template <int D, int P, typename S, typename STT>
+__device__ __forceinline__ void prefetch_box(const CUtensorMap* maps4, const StepArgs& a, const STT& st, int plane,
+                                             int tile) {
+  while (plane >= a.planes) {
+    plane -= a.planes;
+    tile += gridDim.x;
   }
+  if (tile >= a.ntiles) return;
+  int X, Y, Z;
+  const int v = box_origin<D, P, S>(a, st, plane, tile, X, Y, Z);
+  tma_prefetch_4d(&maps4[v], X, Y, Z, plane);
 }
 
 // ---------------------------------------------------------------------------
-// separable passes
+// separable passes on 4-element x groups
 // ---------------------------------------------------------------------------
+// z pass: box [TZ+P][BYA][BXW] (S) -> bufA [TZ][BYA][BXW] (C)
 template <int D, int P, typename S, int BYA>
-__device__ __forceinline__ void zpass(const S* box, typename Store<S>::C* bufA, const typename Store<S>::C* Wz) {
+__device__ __forceinline__ void zpass(const S* box, typename Store<S>::C* bufA, const typename Store<S>::C* W) {
   using L = Layout<D, P, S>;
   using C = typename Store<S>::C;
-  constexpr int COLS = BYA * L::BXW;
-  for (int col = threadIdx.x; col < COLS; col += NT) {
-    C v[L::TZ + P];
+  constexpr int ZCH = 2, NZC = L::TZ / ZCH;
+  constexpr int ITEMS = L::NQX * BYA * NZC;
+  constexpr int PL = BYA * L::BXW;
+  for (int item = threadIdx.x; item < ITEMS; item += NT) {
+    const int q = item % L::NQX, r = item / L::NQX, y = r % BYA, zc = r / BYA;
+    const int off = (zc * ZCH * BYA + y) * L::BXW + 4 * q;
+    C v[ZCH + P][4];
 #pragma unroll
-    for (int k = 0; k < L::TZ + P; ++k) v[k] = Store<S>::ld(box[k * L::PL + col]);
+    for (int k = 0; k < ZCH + P; ++k) ld4(box + off + k * PL, v[k]);
 #pragma unroll
-    for (int z = 0; z < L::TZ; ++z) {
-      C acc = Wz[0] * v[z];
+    for (int z = 0; z < ZCH; ++z) {
+      C o[4];
 #pragma unroll
-      for (int k = 1; k <= P; ++k) acc = fma(Wz[k], v[z + k], acc);
-      bufA[z * L::PL + col] = acc;
+      for (int e = 0; e < 4; ++e) {
+        C acc = W[0] * v[z][e];
+#pragma unroll
+        for (int k = 1; k <= P; ++k) acc = fma(W[k], v[z + k][e], acc);
+        o[e] = acc;
+      }
+      st4(bufA + off + z * PL, o);
     }
   }
 }
 
-template <int D, int P, typename S, typename SRC, typename LD>
-__device__ __forceinline__ void ypass(const SRC* src, typename Store<S>::C* bufB, const typename Store<S>::C* Wy,
-                                      LD ld) {
+// y pass: src [TZ][BY][BXW] (S box or C bufA) -> bufB [TZ][TY][BXW] (C)
+template <int D, int P, typename S, typename SRC>
+__device__ __forceinline__ void ypass(const SRC* src, typename Store<S>::C* bufB, const typename Store<S>::C* W) {
   using L = Layout<D, P, S>;
   using C = typename Store<S>::C;
-  constexpr int YCH = 8, NCH = L::TY / YCH;
-  constexpr int ITEMS = L::TZ * NCH * L::BXW;
+  constexpr int YCH = 2, NYC = L::TY / YCH;
+  constexpr int ITEMS = L::NQX * L::TZ * NYC;
   for (int item = threadIdx.x; item < ITEMS; item += NT) {
-    const int x = item % L::BXW, r = item / L::BXW, ch = r % NCH, z = r / NCH;
-    const SRC* s = src + (z * L::BY + ch * YCH) * L::BXW + x;
-    C v[YCH + P];
+    const int q = item % L::NQX, r = item / L::NQX, yc = r % NYC, z = r / NYC;
+    const SRC* s = src + (z * L::BY + yc * YCH) * L::BXW + 4 * q;
+    C v[YCH + P][4];
 #pragma unroll
-    for (int k = 0; k < YCH + P; ++k) v[k] = ld(s[k * L::BXW]);
-    C* o = bufB + (z * L::TY + ch * YCH) * L::BXW + x;
+    for (int k = 0; k < YCH + P; ++k) ld4(s + k * L::BXW, v[k]);
+    C* o = bufB + (z * L::TY + yc * YCH) * L::BXW + 4 * q;
 #pragma unroll
     for (int y = 0; y < YCH; ++y) {
-      C acc = Wy[0] * v[y];
+      C w4[4];
 #pragma unroll
-      for (int k = 1; k <= P; ++k) acc = fma(Wy[k], v[y + k], acc);
-      o[y * L::BXW] = acc;
+      for (int e = 0; e < 4; ++e) {
+        C acc = W[0] * v[y][e];
+#pragma unroll
+        for (int k = 1; k <= P; ++k) acc = fma(W[k], v[y + k][e], acc);
+        w4[e] = acc;
+      }
+      st4(o + y * L::BXW, w4);
     }
   }
 }
 
-template <int D, int P, typename S, int PY, typename SRC, typename LD>
-__device__ __forceinline__ void xpass(const SRC* src, int xo, bool xact, const typename Store<S>::C* Wx,
-                                      typename Store<S>::C out[NPT], LD ld) {
+// x pass into the thread's four nodes: src [..][TY][BXW]; XO = first needed
+// column of the group inside the 16-byte aligned box row.
+template <int D, int P, typename S, int XO, bool XACT, typename SRC>
+__device__ __forceinline__ void xpass(const SRC* src, int qx, int ly, int lz, const typename Store<S>::C* W,
+                                      typename Store<S>::C out[4]) {
   using L = Layout<D, P, S>;
   using C = typename Store<S>::C;
-#pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    int lx, ly, lz;
-    node_of<D>(k, lx, ly, lz);
-    const SRC* s = src + (lz * PY + ly) * L::BXW + xo + lx;
-    if (xact) {
-      C acc = Wx[0] * ld(s[0]);
-#pragma unroll
-      for (int j = 1; j <= P; ++j) acc = fma(Wx[j], ld(s[j]), acc);
-      out[k] = acc;
-    } else {
-      out[k] = ld(s[0]);
-    }
+  const SRC* s = src + (lz * L::TY + ly) * L::BXW + qx;
+  if (!XACT) {
+    ld4(s, out);
+    return;
   }
+  constexpr int NQ = (XO + 3 + P) / 4 + 1;
+  C v[NQ * 4];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) ld4(s + 4 * k, &v[4 * k]);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    C acc = W[0] * v[XO + e];
+#pragma unroll
+    for (int j = 1; j <= P; ++j) acc = fma(W[j], v[XO + e + j], acc);
+    out[e] = acc;
+  }
+}
+
+template <int D, int P, typename S, typename SRC, int XO>
+__device__ __forceinline__ void xpass_dispatch_rec(int xo, const SRC* src, int qx, int ly, int lz,
+                                                   const typename Store<S>::C* W, typename Store<S>::C out[4]) {
+  if constexpr (XO < Layout<D, P, S>::VEC) {
+    if (xo == XO) {
+      xpass<D, P, S, XO, true>(src, qx, ly, lz, W, out);
+      return;
+    }
+    xpass_dispatch_rec<D, P, S, SRC, XO + 1>(xo, src, qx, ly, lz, W, out);
+  }
+}
+
+template <int D, int P, typename S, typename SRC>
+__device__ __forceinline__ void xpass_any(bool xact, int xo, const SRC* src, int qx, int ly, int lz,
+                                          const typename Store<S>::C* W, typename Store<S>::C out[4]) {
+  if (!xact) {
+    xpass<D, P, S, 0, false>(src, qx, ly, lz, W, out);
+    return;
+  }
+  xpass_dispatch_rec<D, P, S, SRC, 0>(xo, src, qx, ly, lz, W, out);
+}
+
+// ---------------------------------------------------------------------------
+// periodic copies of a node in the ghost layers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int first_image(int c, int n, int gl) {
+  return c - n * ((c + gl) / n);  // smallest c + k n that is >= -gl
+}
+
+// Store one value at node (x, y, z) and at every periodic copy of it that
+// falls in the ghost layers.
+template <typename S>
+__device__ void store_all_images(S* plane, const Padded& P, int x, int y, int z, S v) {
+  for (int cz = first_image(z, P.n[2], P.gl[2]); cz < P.n[2] + P.gr[2]; cz += P.n[2])
+    for (int cy = first_image(y, P.n[1], P.gl[1]); cy < P.n[1] + P.gr[1]; cy += P.n[1])
+      for (int cx = first_image(x, P.n[0], P.gl[0]); cx < P.n[0] + P.gr[0]; cx += P.n[0])
+        plane[pad_index(P, cx, cy, cz)] = v;
+}
+
+// Copies (excluding the node itself) of a 4-node x group whose x coordinate
+// and every ghost width are multiples of 4 (n[0] % 4 == 0).
+template <typename S, typename C>
+__device__ void store_group_images(S* plane, const Padded& P, int x, int y, int z, const C v[4]) {
+  for (int cz = first_image(z, P.n[2], P.gl[2]); cz < P.n[2] + P.gr[2]; cz += P.n[2])
+    for (int cy = first_image(y, P.n[1], P.gl[1]); cy < P.n[1] + P.gr[1]; cy += P.n[1])
+      for (int cx = first_image(x, P.n[0], P.gl[0]); cx < P.n[0] + P.gr[0]; cx += P.n[0])
+        if (cx != x || cy != y || cz != z) st4(plane + pad_index(P, cx, cy, cz), v);
 }
 
 // ---------------------------------------------------------------------------
@@ -271,65 +453,79 @@ __device__ __forceinline__ void xpass(const SRC* src, int xo, bool xact, const t
 template <int D, int P, typename S, bool COMP>
 __global__ void __launch_bounds__(NT, 1)
     sl_step_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
-                   const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st) {
+                   const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
+                   const __grid_constant__ TmaMaps maps) {
   using L = Layout<D, P, S>;
   using C = typename Store<S>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* boxes = reinterpret_cast<S*>(smem_raw);
-  C* bufA = reinterpret_cast<C*>(smem_raw + 2 * (size_t)L::BOX * sizeof(S));
-  C* bufB = bufA + L::BUFA;
-  double* red_smem = reinterpret_cast<double*>(bufB + L::BUFB);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
+  S* boxes[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + L::BOXB)};
+  C* bufA = reinterpret_cast<C*>(base + L::OFF_A);
+  C* bufB = reinterpret_cast<C*>(base + L::OFF_B);
+  double* red_smem = reinterpret_cast<double*>(base + L::OFF_R);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base + L::OFF_M);
 
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = a.Q, planes = a.planes;
-  C* scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE;
-  S* dst = static_cast<S*>(a.dst);
-  const auto ldS = [](S v) { return Store<S>::ld(v); };
-  const auto ldC = [](C v) { return v; };
+  const Padded& pd = a.pad;
+  const CUtensorMap* maps4 = maps.m[a.src];
+  S* dst = static_cast<S*>(a.buf[a.src ^ 1]);
+  C* scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE + 4 * tid;
 
-  double red[NRED];
-#pragma unroll
-  for (int q = 0; q < NRED; ++q) red[q] = 0.0;
+  // this thread's nodes: x = qx..qx+3, row ly, layer lz of the tile
+  const int qx = (tid & 7) * 4;
+  const int ly = D == 3 ? ((tid >> 3) & 7) : (tid >> 3);
+  const int lz = D == 3 ? (tid >> 6) : 0;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (tid < (NT / 32) * NRED) red_smem[tid] = 0.0;  // per-warp FP64 totals
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < a.ntiles) {
+    issue_box<D, P, S>(boxes[0], &bars[0], maps4, a, st, 0, blockIdx.x);
+    for (int k = 1; k < PREFETCH; ++k) prefetch_box<D, P, S>(maps4, a, st, k, blockIdx.x);
+  }
+  const unsigned long long keep = policy_evict_last(), stream_out = policy_evict_first();
 
   int buf = 0;
-  if ((int)blockIdx.x < a.ntiles) {
-    stage_plane<D, P, S, VelTab<C>, StencilTab<C, P + 1>>(boxes, a, st, 0, blockIdx.x);
-    cp_async_commit();
-  }
+  unsigned parity = 0;  // bit b: phase of bars[b]
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int tx = tile % a.nt[0], tr = tile / a.nt[0];
     const int ty = tr % a.nt[1], tz = tr / a.nt[1];
-    const int x0 = tx * L::TX, y0 = ty * L::TY, z0 = tz * L::TZ;
+    const int x0 = tx * L::TX + qx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
 
-    C Ad[NPT], jx[NPT], jy[NPT], jz[NPT];
-    C Bp[NPT], Gp[NPT];          // compressible: per-group partial sums
-    double Bd[NPT], Gd[NPT];     // compressible: FP64 totals
+    C Ad[4], jx[4], jy[4], jz[4], Bp[4], Gp[4];
+    double Bd[4], Gd[4];
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      Ad[k] = jx[k] = jy[k] = jz[k] = C(0);
-      Bp[k] = Gp[k] = C(0);
-      Bd[k] = Gd[k] = 0.0;
+    for (int e = 0; e < 4; ++e) {
+      Ad[e] = jx[e] = jy[e] = jz[e] = Bp[e] = Gp[e] = C(0);
+      Bd[e] = Gd[e] = 0.0;
     }
 
     for (int p = 0; p < planes; ++p) {
-      S* box = boxes + buf * L::BOX;
-      if (a.vec_ok) {
-        cp_async_wait_all();
-        __syncthreads();
-        // stream the next plane (or the next tile's first plane) in behind this one
-        if (p + 1 < planes) {
-          stage_plane<D, P, S, VelTab<C>, StencilTab<C, P + 1>>(boxes + (buf ^ 1) * L::BOX, a, st, p + 1, tile);
-        } else if (tile + (int)gridDim.x < a.ntiles) {
-          stage_plane<D, P, S, VelTab<C>, StencilTab<C, P + 1>>(boxes + (buf ^ 1) * L::BOX, a, st, 0,
-                                                                tile + gridDim.x);
-        }
-        cp_async_commit();
-      } else {
-        __syncthreads();
-        if (p > 0 || tile != (int)blockIdx.x)
-          stage_plane<D, P, S, VelTab<C>, StencilTab<C, P + 1>>(box, a, st, p, tile);
-        __syncthreads();
+      const bool ok = mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u);
+        return;
       }
-
+      parity ^= 1u << buf;
+      if (tid == 0) {
+        int np_ = p + 1, nt_ = tile;
+        if (np_ == planes) {
+          np_ = 0;
+          nt_ = tile + gridDim.x;
+        }
+        if (nt_ < a.ntiles) {
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          issue_box<D, P, S>(boxes[buf ^ 1], &bars[buf ^ 1], maps4, a, st, np_, nt_);
+        }
+        prefetch_box<D, P, S>(maps4, a, st, p + PREFETCH, tile);
+      }
+      const S* box = boxes[buf];
       const int i = p < Q ? p : p - Q;
       const int act = st.active[i];
       C Wx[P + 1], Wy[P + 1], Wz[P + 1];
@@ -339,27 +535,28 @@ __global__ void __launch_bounds__(NT, 1)
         Wy[j] = st.W[i][1][j];
         Wz[j] = D == 3 ? st.W[i][2][j] : C(0);
       }
-      const int gxs = x0 + ((act & 1) ? st.m0[i][0] : 0);
-      const int xo = wrap_mod(gxs, L::VEC);
+      const bool xact = act & 1;
+      const int xo = xact ? ((st.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
 
-      C out[NPT];
+      C out[4];
       if (D == 3 && (act & 4)) {
-        if (act & 2) zpass<D, P, S, L::TY + P>(box, bufA, Wz);
-        else zpass<D, P, S, L::TY>(box, bufA, Wz);
-        __syncthreads();
         if (act & 2) {
-          ypass<D, P, S>(bufA, bufB, Wy, ldC);
+          zpass<D, P, S, L::BY>(box, bufA, Wz);
           __syncthreads();
-          xpass<D, P, S, L::TY>(bufB, xo, act & 1, Wx, out, ldC);
+          ypass<D, P, S>(static_cast<const C*>(bufA), bufB, Wy);
+          __syncthreads();
+          xpass_any<D, P, S>(xact, xo, static_cast<const C*>(bufB), qx, ly, lz, Wx, out);
         } else {
-          xpass<D, P, S, L::BY>(bufA, xo, act & 1, Wx, out, ldC);
+          zpass<D, P, S, L::TY>(box, bufA, Wz);
+          __syncthreads();
+          xpass_any<D, P, S>(xact, xo, static_cast<const C*>(bufA), qx, ly, lz, Wx, out);
         }
       } else if (act & 2) {
-        ypass<D, P, S>(box, bufB, Wy, ldS);
+        ypass<D, P, S>(box, bufB, Wy);
         __syncthreads();
-        xpass<D, P, S, L::TY>(bufB, xo, act & 1, Wx, out, ldC);
+        xpass_any<D, P, S>(xact, xo, static_cast<const C*>(bufB), qx, ly, lz, Wx, out);
       } else {
-        xpass<D, P, S, L::BY>(box, xo, act & 1, Wx, out, ldS);
+        xpass_any<D, P, S>(xact, xo, box, qx, ly, lz, Wx, out);
       }
       buf ^= 1;
 
@@ -368,143 +565,177 @@ __global__ void __launch_bounds__(NT, 1)
         const C cx = vt.xi[i][0], cy = vt.xi[i][1], cz = D == 3 ? vt.xi[i][2] : C(0);
         const C c2 = vt.xi2[i];
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-          Ad[k] += out[k];
-          jx[k] = fma(cx, out[k], jx[k]);
-          jy[k] = fma(cy, out[k], jy[k]);
-          if (D == 3) jz[k] = fma(cz, out[k], jz[k]);
-          if (COMP) Bp[k] = fma(c2, out[k], Bp[k]);
+        for (int e = 0; e < 4; ++e) {
+          Ad[e] += out[e];
+          jx[e] = fma(cx, out[e], jx[e]);
+          jy[e] = fma(cy, out[e], jy[e]);
+          if (D == 3) jz[e] = fma(cz, out[e], jz[e]);
+          if (COMP) Bp[e] = fma(c2, out[e], Bp[e]);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) Gp[k] += out[k];
+        for (int e = 0; e < 4; ++e) Gp[e] += out[e];
       }
       if (COMP && ((p & 7) == 7 || p == planes - 1)) {
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-          Bd[k] += (double)Bp[k];
-          Gd[k] += (double)Gp[k];
-          Bp[k] = Gp[k] = C(0);
+        for (int e = 0; e < 4; ++e) {
+          Bd[e] += (double)Bp[e];
+          Gd[e] += (double)Gp[e];
+          Bp[e] = Gp[e] = C(0);
         }
       }
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) scr[p * L::TILE + threadIdx.x + NT * k] = out[k];
+      gst4(scr + (size_t)p * L::TILE, out, keep);
     }
 
     // ---- collision: equilibrium (Appendix A) and BGK (Sec. 3) -------------
-    C rho[NPT], uhx[NPT], uhy[NPT], uhz[NPT], q[NPT], itau[NPT], tt[NPT], gA[NPT], rth[NPT];
-    C Pi[NPT][6];
-    bool inside[NPT];
-    long long gidx[NPT];
+    const bool yz_in = y < pd.n[1] && z < pd.n[2];
+    bool vin[4];
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int lx, ly, lz;
-      node_of<D>(k, lx, ly, lz);
-      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-      inside[k] = gx < a.n[0] && gy < a.n[1] && gz < a.n[2];
-      gidx[k] = ((long long)gz * a.n[1] + gy) * a.n[0] + gx;
-      rho[k] = C(a.rho_ref) + Ad[k];
-      const C ir = C(1) / rho[k];
-      const C ux = jx[k] * ir, uy = jy[k] * ir, uz = jz[k] * ir;
-      const C ics = C(a.inv_cs);
-      uhx[k] = ux * ics;
-      uhy[k] = uy * ics;
-      uhz[k] = uz * ics;
-      q[k] = uhx[k] * uhx[k] + uhy[k] * uhy[k] + uhz[k] * uhz[k];
-      double theta = 1.0, tau = a.tau;
+    for (int e = 0; e < 4; ++e) vin[e] = yz_in && (x0 + e) < pd.n[0];
+    const bool group = a.quad_ok && vin[0];
+    const bool images = yz_in && (x0 < pd.gr[0] || x0 + 4 > pd.n[0] - pd.gl[0] || y < pd.gr[1] ||
+                                  y >= pd.n[1] - pd.gl[1] || z < pd.gr[2] || z >= pd.n[2] - pd.gl[2]);
+    const long long main_off = pad_index(pd, x0, y, z);
+
+    C rho[4], uhx[4], uhy[4], uhz[4], q[4], itau[4], tt[4], gA[4], rth[4], Pi[4][6];
+    C rtheta[4], rtau[4];
+    const C ics = C(a.inv_cs);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      rho[e] = C(a.rho_ref) + Ad[e];
+      const C ir = C(1) / rho[e];
+      uhx[e] = jx[e] * ir * ics;
+      uhy[e] = jy[e] * ir * ics;
+      uhz[e] = jz[e] * ir * ics;
+      q[e] = uhx[e] * uhx[e] + uhy[e] * uhy[e] + uhz[e] * uhz[e];
       if (COMP) {
-        const double r = (double)rho[k];
-        const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-        const double thm1 = (Bd[k] + Gd[k] - r * u2 - a.two_cv * (double)Ad[k]) / (a.two_cv * r);
-        theta = 1.0 + thm1;
-        tau = a.mu_dt / (r * theta) + 0.5;
-        itau[k] = C(1.0 / tau);
-        tt[k] = C(thm1);
-        gA[k] = C(r * thm1 + (double)Ad[k]);
-        rth[k] = C(r * theta);
+        // temperature relation (Sec. 3) in FP64: energy minus kinetic part cancels
+        const double r = (double)rho[e];
+        const double jj = (double)jx[e] * jx[e] + (double)jy[e] * jy[e] + (double)jz[e] * jz[e];
+        const double X = Bd[e] + Gd[e] - jj / r - a.two_cv * (double)Ad[e];
+        const C thm1 = C(X) / (C(a.two_cv) * rho[e]);
+        const C theta = C(1) + thm1;
+        const C tau = C(a.mu_dt) / (rho[e] * theta) + C(0.5);
+        itau[e] = C(1) / tau;
+        tt[e] = thm1;
+        gA[e] = fma(rho[e], thm1, Ad[e]);
+        rth[e] = rho[e] * theta;
+        rtheta[e] = theta;
+        rtau[e] = tau;
       } else {
-        itau[k] = C(a.inv_tau);
-        tt[k] = C(0);
-        gA[k] = rth[k] = C(0);
+        itau[e] = C(a.inv_tau);
+        tt[e] = gA[e] = rth[e] = C(0);
+        rtheta[e] = C(1);
+        rtau[e] = C(a.tau);
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c) Pi[k][c] = C(0);
-      if (inside[k]) {
-        const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-        red[0] += 0.5 * u2;
-        red[1] += 0.5 * (double)rho[k] * u2;
-        red[3] += (double)rho[k];
-        red[4] += (double)jx[k];
-        red[5] += (double)jy[k];
-        red[6] += (double)jz[k];
-        const bool fin = isfinite((double)rho[k]) && isfinite((double)ux) && isfinite((double)uy) &&
-                         isfinite((double)uz) && isfinite(theta);
-        red[7] += fin ? 0.0 : 1.0;
-        // tau and theta are needed again for the dissipation estimate below
-        Bd[k] = theta;
-        Gd[k] = tau;
-      }
+      for (int c = 0; c < 6; ++c) Pi[e][c] = C(0);
     }
 
-    for (int i = 0; i < Q; ++i) {
-      const C wi = vt.w[i], xhx = vt.xih[i][0], xhy = vt.xih[i][1], xhz = D == 3 ? vt.xih[i][2] : C(0);
-      const C rD = vt.rD[i], rp = vt.rpoly[i];
-      C xx[6];
+    const bool red = a.reduce != 0;
+    // velocities in batches: the staging loads of a batch are all in flight
+    // before the first one is used
+    constexpr int BATCH = COMP ? 4 : 8;
+    for (int i0 = 0; i0 < Q; i0 += BATCH) {
+      C v[BATCH][4], vg[BATCH][4];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) xx[c] = vt.xx[i][c];
-      C v[NPT], vg[NPT];
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        v[k] = scr[i * L::TILE + threadIdx.x + NT * k];
-        if (COMP) vg[k] = scr[(Q + i) * L::TILE + threadIdx.x + NT * k];
+      for (int b = 0; b < BATCH; ++b) {
+        if (i0 + b >= Q) break;
+        gld4(scr + (size_t)(i0 + b) * L::TILE, v[b], keep);
+        if (COMP) gld4(scr + (size_t)(Q + i0 + b) * L::TILE, vg[b], keep);
       }
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        const C s = fma(xhx, uhx[k], fma(xhy, uhy[k], xhz * uhz[k]));
-        const C ph = phi_m1<C, COMP>(s, q[k], tt[k], rD, rp, a.N);
-        const C feqd = wi * fma(rho[k], ph, Ad[k]);
-        const C fneq = v[k] - feqd;
-        const C post = fma(-fneq, itau[k], v[k]);
-        if (inside[k]) dst[(long long)i * a.nnodes + gidx[k]] = Store<S>::st(post);
+      for (int b = 0; b < BATCH; ++b) {
+        const int i = i0 + b;
+        if (i >= Q) break;
+        const C wi = vt.w[i], xhx = vt.xih[i][0], xhy = vt.xih[i][1], xhz = D == 3 ? vt.xih[i][2] : C(0);
+        const C rD = vt.rD[i], rp = vt.rpoly[i];
+        C o[4], og[4], fneq[4];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) Pi[k][c] = fma(xx[c], fneq, Pi[k][c]);
-        if (COMP) {
-          const C geqd = wi * C(a.gfac) * fma(rth[k], ph, gA[k]);
-          const C gpost = fma(-(vg[k] - geqd), itau[k], vg[k]);
-          if (inside[k]) dst[(long long)(Q + i) * a.nnodes + gidx[k]] = Store<S>::st(gpost);
+        for (int e = 0; e < 4; ++e) {
+          const C s = fma(xhx, uhx[e], fma(xhy, uhy[e], xhz * uhz[e]));
+          const C ph = phi_m1<C, COMP>(s, q[e], tt[e], rD, rp, a.N);
+          const C feqd = wi * fma(rho[e], ph, Ad[e]);
+          fneq[e] = v[b][e] - feqd;
+          o[e] = fma(-fneq[e], itau[e], v[b][e]);
+          if (COMP) {
+            const C geqd = wi * C(a.gfac) * fma(rth[e], ph, gA[e]);
+            og[e] = fma(-(vg[b][e] - geqd), itau[e], vg[b][e]);
+          }
+        }
+        S* pf = dst + (long long)i * pd.plane;
+        S* pg = dst + (long long)(Q + i) * pd.plane;
+        if (group) {
+          gst4(pf + main_off, o, stream_out);
+          if (COMP) gst4(pg + main_off, og, stream_out);
+          if (images) {
+            store_group_images(pf, pd, x0, y, z, o);
+            if (COMP) store_group_images(pg, pd, x0, y, z, og);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!vin[e]) continue;
+            store_all_images(pf, pd, x0 + e, y, z, Store<S>::st(o[e]));
+            if (COMP) store_all_images(pg, pd, x0 + e, y, z, Store<S>::st(og[e]));
+          }
+        }
+        if (red) {
+          C xx[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) xx[c] = vt.xx[i][c];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Pi[e][c] = fma(xx[c], fneq[e], Pi[e][c]);
         }
       }
     }
+
+    if (red) {
+      // per-thread sums over its nodes, then per warp, then FP64 per warp and tile
+      C t[NRED];
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      if (!inside[k]) continue;
-      const double theta = COMP ? Bd[k] : 1.0, tau = COMP ? Gd[k] : a.tau;
-      const double pres = (double)rho[k] * theta * a.cs2;
-      const double den = 2.0 * pres * tau * a.dt;
-      const double ss = ((double)Pi[k][0] * Pi[k][0] + (double)Pi[k][1] * Pi[k][1] +
-                         (double)Pi[k][2] * Pi[k][2] +
-                         2.0 * ((double)Pi[k][3] * Pi[k][3] + (double)Pi[k][4] * Pi[k][4] +
-                                (double)Pi[k][5] * Pi[k][5])) /
-                        (den * den);
-      const double nu = a.cs2 * theta * a.dt * (tau - 0.5);
-      red[2] += 2.0 * nu * ss;
+      for (int c = 0; c < NRED; ++c) t[c] = C(0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (!vin[e]) continue;
+        const C u2 = q[e] * C(a.cs2);
+        t[0] += C(0.5) * u2;
+        t[1] += C(0.5) * rho[e] * u2;
+        t[3] += Ad[e];
+        t[4] += jx[e];
+        t[5] += jy[e];
+        t[6] += jz[e];
+        const bool fin = isfinite(rho[e]) && isfinite(uhx[e]) && isfinite(uhy[e]) && isfinite(uhz[e]) &&
+                         isfinite(rtheta[e]);
+        t[7] += fin ? C(0) : C(1);
+        const C pres = rho[e] * rtheta[e] * C(a.cs2);
+        const C den = C(2) * pres * rtau[e] * C(a.dt);
+        const C ss = (Pi[e][0] * Pi[e][0] + Pi[e][1] * Pi[e][1] + Pi[e][2] * Pi[e][2] +
+                      C(2) * (Pi[e][3] * Pi[e][3] + Pi[e][4] * Pi[e][4] + Pi[e][5] * Pi[e][5])) /
+                     (den * den);
+        const C nu = C(a.cs2) * rtheta[e] * C(a.dt) * (rtau[e] - C(0.5));
+        t[2] += C(2) * nu * ss;
+      }
+#pragma unroll
+      for (int c = 0; c < NRED; ++c) {
+        C v = t[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red_smem[warp * NRED + c] += (double)v;
+      }
     }
   }
 
   // ---- per-CTA FP64 partials, fixed order -----------------------------------
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NRED; ++q) {
-    double v = red[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red_smem[warp * NRED + q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < NRED) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red_smem[w * NRED + threadIdx.x];
-    a.partials[(size_t)blockIdx.x * NRED + threadIdx.x] = s;
+  if (a.reduce) {
+    __syncthreads();
+    if (tid < NRED) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red_smem[w * NRED + tid];
+      a.partials[(size_t)blockIdx.x * NRED + tid] = s;
+    }
   }
 }
 
@@ -524,7 +755,7 @@ int launch_one(const StepLaunch& L) {
   }
   const auto& vt = *static_cast<const VelTab<C>*>(L.veltab);
   const auto& st = *static_cast<const StencilTab<C, P + 1>*>(L.stentab);
-  kern<<<L.grid, NT, Lay::BYTES, static_cast<cudaStream_t>(L.stream)>>>(L.a, vt, st);
+  kern<<<L.grid, NT, Lay::BYTES, static_cast<cudaStream_t>(L.stream)>>>(L.a, vt, st, *L.maps);
   return (int)cudaGetLastError();
 }
 
@@ -532,21 +763,25 @@ template <int D, int P, typename S, bool COMP>
 int occupancy_one(size_t* smem) {
   using Lay = Layout<D, P, S>;
   auto kern = sl_step_kernel<D, P, S, COMP>;
+  *smem = Lay::BYTES;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES) != cudaSuccess)
     return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, Lay::BYTES) != cudaSuccess) return 0;
-  *smem = Lay::BYTES;
   return n;
 }
 
 template <int D, int P, typename S>
-void layout_of(int* bxw, int* by, int* bz, int* tile) {
+void layout_of(StepInfo* o) {
   using Lay = Layout<D, P, S>;
-  *bxw = Lay::BXW;
-  *by = Lay::BY;
-  *bz = Lay::BZ;
-  *tile = Lay::TILE;
+  o->bxw = Lay::BXW;
+  o->by = Lay::BY;
+  o->bz = Lay::BZ;
+  o->tile = Lay::TILE;
+  o->tx = Lay::TX;
+  o->ty = Lay::TY;
+  o->tz = Lay::TZ;
+  o->vec = Lay::VEC;
 }
 
 }  // namespace olb

@@ -1,5 +1,5 @@
-// Instantiations of the fused step for __half storage (generated list of the
-// dimensions and interpolation degrees that are built).
+// Instantiations of the fused step for __half storage: the dimensions and
+// interpolation degrees that are built.
 #include "olb_step.cuh"
 
 namespace olb {
@@ -24,32 +24,32 @@ int launch_step_f16(const StepLaunch& L) {
 int step_info_f16(int D, int P, int comp, StepInfo* out) {
   using S = __half;
   if (D == 2 && P == 2) {
-    layout_of<2, 2, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<2, 2, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<2, 2, S, true>(&out->smem) : occupancy_one<2, 2, S, false>(&out->smem);
     return 0;
   }
   if (D == 2 && P == 3) {
-    layout_of<2, 3, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<2, 3, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<2, 3, S, true>(&out->smem) : occupancy_one<2, 3, S, false>(&out->smem);
     return 0;
   }
   if (D == 2 && P == 4) {
-    layout_of<2, 4, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<2, 4, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<2, 4, S, true>(&out->smem) : occupancy_one<2, 4, S, false>(&out->smem);
     return 0;
   }
   if (D == 3 && P == 2) {
-    layout_of<3, 2, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<3, 2, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 2, S, true>(&out->smem) : occupancy_one<3, 2, S, false>(&out->smem);
     return 0;
   }
   if (D == 3 && P == 3) {
-    layout_of<3, 3, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<3, 3, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 3, S, true>(&out->smem) : occupancy_one<3, 3, S, false>(&out->smem);
     return 0;
   }
   if (D == 3 && P == 4) {
-    layout_of<3, 4, S>(&out->bxw, &out->by, &out->bz, &out->tile);
+    layout_of<3, 4, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 4, S, true>(&out->smem) : occupancy_one<3, 4, S, false>(&out->smem);
     return 0;
   }
