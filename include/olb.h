@@ -174,6 +174,30 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);
 /* Wait for the handle's stream, polling with a bound of timeout_ms (<= 0: no bound). */
 int olb_synchronize(olb_handle h, int timeout_ms);
 
+/* Global sums of a state held by the caller, computed without allocating.
+ * No counterpart in the paper: this is for callers that cannot allocate device
+ * memory at the point where they need the sums (a framework that owns all
+ * device memory through its own pool, or a loop that must not pay for
+ * cudaMalloc's implicit synchronisation).  The per-block partial sums live in a
+ * fixed array inside the library image (OLB_NOALLOC_MAX_BLOCKS x 8 doubles =
+ * 128 KiB on every GPU that loads the library, kept until the process exits),
+ * so the call allocates nothing.
+ *   populations: device pointer, [Q][nz][ny][nx] storage values (the layout of
+ *                olb_get_state for an isothermal state: shifted by w_i rho0
+ *                unless storage is OLB_FP64);
+ *   out:         device pointer to 8 doubles, filled like olb_reductions()
+ *                with out[2] = NaN (no dissipation estimate without a step);
+ *   stream:      cudaStream_t or NULL; the call only enqueues work on it.
+ * Grids of more than OLB_NOALLOC_MAX_BLOCKS * OLB_NOALLOC_NODES_PER_BLOCK nodes
+ * are rejected with OLB_EBOUNDS.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the array and each overwrites
+ * the slots it uses, so calls whose kernels overlap on the GPU race. */
+#define OLB_NOALLOC_MAX_BLOCKS 2048
+#define OLB_NOALLOC_NODES_PER_BLOCK 65536
+int olb_state_sums_noalloc(int velocity_set, const olb_grid* grid, int storage, double cs_scale,
+                           double rho0, const void* populations, double* out, void* stream);
+
 /* Message for an error code, and the calling thread's most recent failure. */
 const char* olb_strerror(int code);
 const char* olb_last_error(void);

@@ -34,6 +34,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 }  // namespace
 
+void olb::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct olb_ctx {
   olb_grid grid{};
   int vs_id = 0, N = 2, p = 3, storage = 0, comp = 0, allow_inexact = 0;

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 namespace olb {
 
@@ -22,6 +23,9 @@ struct VelocitySet {
 
 // Fill *vs with the unscaled table of set `id` (olb_velocity_set); -1 if unknown.
 int velocity_set(int id, VelocitySet* vs);
+
+// Message returned by olb_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
 
 // Device layout of one population plane: the interior n[0] x n[1] x n[2]
 // nodes surrounded by ghost layers (gl on the low side, gr on the high side of

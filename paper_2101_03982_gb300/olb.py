@@ -67,6 +67,7 @@ def lib():
             "olb_get_state": (i, [vp, vp, sz, i]),
             "olb_set_state": (i, [vp, vp, sz, i]),
             "olb_synchronize": (i, [vp, i]),
+            "olb_state_sums_noalloc": (i, [i, ctypes.POINTER(Grid), i, d, d, vp, vp, vp]),
             "olb_strerror": (ctypes.c_char_p, [i]),
             "olb_last_error": (ctypes.c_char_p, []),
         }
