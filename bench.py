@@ -149,7 +149,8 @@ def make_sim(w, torch):
         return sim, w["n"] ** 2
     rp = params.tgv_isothermal(w["velocity_set"], w["n"], w["Re"], w["Ma"], w["courant"])
     sim = olb.Sim((w["n"],) * 3, rp.dx, w["velocity_set"], w["N"], rp.tau, rp.dt, interp_order=w["p"],
-                  storage=w["storage"], cs_scale=rp.cs_scale, log_every=w.get("log_every", 10))
+                  storage=w["storage"], cs_scale=rp.cs_scale, log_every=w.get("log_every", 10),
+                  kernel=w.get("kernel", "auto"))
     rho, u = inputs.tgv3d(w["n"], rp.u0, rp.cs ** 2)
     sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
     return sim, w["n"] ** 3
@@ -178,6 +179,7 @@ def per_set_table(torch, flush):
         for st in ("fp32", "bf16", "fp64"):
             specs.append(dict(WORKLOAD, velocity_set=vs, storage=st))
     specs.append(dict(WORKLOAD, velocity_set="D3V27", N=3))
+    specs.append(dict(WORKLOAD, kernel="generic"))
     specs.append(dict(WORKLOAD, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
@@ -199,7 +201,7 @@ def per_set_table(torch, flush):
         t = statistics.mean(ts)
         s = sim.elem_bytes
         nbytes = 2 * sim.planes * s * nodes
-        rows.append(dict(velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
+        rows.append(dict(kernel=w.get("kernel", "auto"), velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
                          N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
                          mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
                          gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))

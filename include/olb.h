@@ -93,13 +93,14 @@ typedef struct {
   double rho0;       /* reference density of the shifted storage (default 1) */
   int allow_inexact; /* 1: accept a quadrature degree below 2N */
   int log_every;     /* the global sums are accumulated on steps whose count is a multiple of this (>= 1) */
+  int kernel;        /* 0: automatic (warp-specialized step where it fits), 1: single-role step kernel */
   void* stream;      /* cudaStream_t for every call of the handle; NULL = default stream */
 } olb_options;
 
 typedef struct olb_ctx* olb_handle;
 
 /* Fill *opt with defaults: p = 3, FP64, cs_scale = 1, isothermal, gamma = 1.4,
- * mu = 0, rho0 = 1, allow_inexact = 0, log_every = 1, stream = NULL. */
+ * mu = 0, rho0 = 1, allow_inexact = 0, log_every = 1, kernel = 0, stream = NULL. */
 void olb_default_options(olb_options* opt);
 
 /* Abscissae count Q, dimension D, c_s, largest |xi_{i,alpha}| and degree of a

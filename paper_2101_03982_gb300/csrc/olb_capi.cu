@@ -14,7 +14,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/olb.h"
+#include "olb.h"
 #include "olb_internal.h"
 
 using namespace olb;
@@ -51,10 +51,12 @@ struct olb_ctx {
   int* err_dev = nullptr;
   int step_grid = 0, partial_slots = 0;
   int log_every = 1;
+  int force_generic = 0;
   long long step_count = 0;
   int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
   Padded pad{};
   TmaMaps maps{};
+  WgSchedule sched{};
   cudaStream_t stream = nullptr;
   int device = 0;
   StepInfo info{};
@@ -77,15 +79,18 @@ int storage_bytes(int storage) {
   }
 }
 
-int step_info(int D, int P, int storage, int comp, StepInfo* out) {
+int step_info(int D, int P, int storage, int comp, int Q, int force_generic, StepInfo* out) {
   switch (storage) {
-    case OLB_FP64: return step_info_f64(D, P, comp, out);
-    case OLB_FP32_SHIFTED: return step_info_f32(D, P, comp, out);
-    case OLB_BF16_SHIFTED: return step_info_bf16(D, P, comp, out);
-    case OLB_FP16_SHIFTED: return step_info_f16(D, P, comp, out);
+    case OLB_FP64:
+      return D == 2 ? step_info_f64_2d(D, P, comp, Q, force_generic, out)
+                    : step_info_f64_3d(D, P, comp, Q, force_generic, out);
+    case OLB_FP32_SHIFTED: return step_info_f32(D, P, comp, Q, force_generic, out);
+    case OLB_BF16_SHIFTED: return step_info_bf16(D, P, comp, Q, force_generic, out);
+    case OLB_FP16_SHIFTED: return step_info_f16(D, P, comp, Q, force_generic, out);
     default: return -1;
   }
 }
+
 
 // Lagrange stencil of degree p around offset delta (grid units): first point
 // m0 and weights W[j] = prod_{k != j} (delta - m_k) / (m_j - m_k).
@@ -195,6 +200,41 @@ void layout_padding(olb_ctx* h) {
   }
   P.plane = (long long)P.np[0] * P.np[1] * P.np[2];
 }
+
+}  // namespace
+
+// Planes of each warpgroup of the two-phase kernel: longest processing time
+// first, with a plane's cost from the passes its velocity needs.
+static void build_schedule(olb_ctx* h) {
+  WgSchedule& S = h->sched;
+  std::memset(&S, 0, sizeof(S));
+  const int nwg = h->info.wg > 0 ? h->info.wg : 1;
+  std::vector<std::pair<double, int>> cost;
+  for (int p = 0; p < h->planes; ++p) {
+    const int i = p % h->Q;
+    double c = 1.0;                                      // x pass (or copy) of every node
+    if (h->set.xi[i][1] != 0.0) c += 1.25;               // y pass
+    if (h->D == 3 && h->set.xi[i][2] != 0.0) c += 1.5;   // z pass
+    cost.push_back({c, p});
+  }
+  std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  double load[4] = {0, 0, 0, 0};
+  std::vector<int> lists[4];
+  for (const auto& cp : cost) {
+    int best = 0;
+    for (int w = 1; w < nwg; ++w)
+      if (load[w] < load[best]) best = w;
+    load[best] += cp.first;
+    lists[best].push_back(cp.second);
+  }
+  for (int w = 0; w < nwg; ++w) {
+    std::sort(lists[w].begin(), lists[w].end());
+    S.n[w] = (int)lists[w].size();
+    for (size_t k = 0; k < lists[w].size(); ++k) S.plane[w][k] = (unsigned char)lists[w][k];
+  }
+}
+
+namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -318,6 +358,7 @@ void olb_default_options(olb_options* opt) {
   opt->rho0 = 1.0;
   opt->allow_inexact = 0;
   opt->log_every = 1;
+  opt->kernel = 0;
   opt->stream = nullptr;
 }
 
@@ -364,6 +405,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   if (!(opt.cs_scale > 0.0) || !std::isfinite(opt.cs_scale)) return fail(OLB_EINVAL, "cs_scale must be positive");
   if (!(opt.rho0 > 0.0)) return fail(OLB_EINVAL, "rho0 must be positive");
   if (opt.log_every < 1) return fail(OLB_EINVAL, "log_every must be >= 1");
+  if (opt.kernel < 0 || opt.kernel > 1) return fail(OLB_EINVAL, "kernel must be 0 (automatic) or 1 (single-role)");
 
   VelocitySet vs;
   if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
@@ -392,6 +434,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->comp = opt.compressible ? 1 : 0;
   h->allow_inexact = opt.allow_inexact;
   h->log_every = opt.log_every;
+  h->force_generic = opt.kernel == 1;
   h->tau = tau;
   h->dt = dt;
   h->gamma = opt.gamma;
@@ -410,7 +453,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->nnodes = nnodes;
   h->stream = static_cast<cudaStream_t>(opt.stream);
 
-  if (step_info(h->D, h->p, h->storage, h->comp, &h->info) != 0) {
+  if (step_info(h->D, h->p, h->storage, h->comp, h->Q, h->force_generic, &h->info) != 0) {
     release(h);
     return fail(OLB_EUNSUPPORTED, "interpolation order not built for this storage");
   }
@@ -440,6 +483,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
     fill_stentab<float>(h);
   }
 
+  build_schedule(h);
   const double Cv = 1.0 / (h->gamma - 1.0);
   const double rho_ref = h->storage == OLB_FP64 ? 0.0 : h->rho0;
   layout_padding(h);
@@ -609,7 +653,9 @@ int olb_step(olb_handle h, int n) {
   L.veltab = h->veltab.data();
   L.stentab = h->stentab.data();
   L.maps = &h->maps;
+  L.sched = &h->sched;
   L.grid = h->step_grid;
+  L.force_generic = h->force_generic;
   L.stream = h->stream;
   for (int s = 0; s < n; ++s) {
     const long long count = h->step_count + 1;
@@ -617,7 +663,7 @@ int olb_step(olb_handle h, int n) {
     L.a.reduce = (count % h->log_every) == 0;
     int r;
     switch (h->storage) {
-      case OLB_FP64: r = launch_step_f64(L); break;
+      case OLB_FP64: r = h->D == 2 ? launch_step_f64_2d(L) : launch_step_f64_3d(L); break;
       case OLB_FP32_SHIFTED: r = launch_step_f32(L); break;
       case OLB_BF16_SHIFTED: r = launch_step_bf16(L); break;
       default: r = launch_step_f16(L); break;
@@ -646,8 +692,10 @@ int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_devi
     du = u ? t + n : nullptr;
     dth = theta ? t + n * (1 + h->D) : nullptr;
   }
-  rc = launch_rc(launch_state_moments(h->aux, h->buf[h->cur], dr, du, dth, nullptr, 1024, h->stream),
-                 "state_moments");
+  rc = check_err(h);
+  if (rc == OLB_OK)
+    rc = launch_rc(launch_state_moments(h->aux, h->buf[h->cur], dr, du, dth, nullptr, 1024, h->stream),
+                   "state_moments");
   if (rc == OLB_OK && !on_device) {
     double* t = static_cast<double*>(tmp);
     if (rho) cudaMemcpyAsync(rho, t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -704,6 +752,8 @@ int olb_get_populations(olb_handle h, double* f, int on_device) {
   if (!h || !f) return fail(OLB_EINVAL, "null handle or buffer");
   int rc = set_device(h);
   if (rc) return rc;
+  rc = check_err(h);
+  if (rc) return rc;
   const size_t bytes = (size_t)h->planes * h->nnodes * sizeof(double);
   double* d = f;
   void* tmp = nullptr;
@@ -755,6 +805,8 @@ int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device) {
   if (!h || !buf) return fail(OLB_EINVAL, "null handle or buffer");
   if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
   int rc = set_device(h);
+  if (rc) return rc;
+  rc = check_err(h);
   if (rc) return rc;
   void* d = buf;
   void* tmp = nullptr;

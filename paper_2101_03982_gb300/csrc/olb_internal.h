@@ -76,6 +76,12 @@ struct TmaMaps {
   CUtensorMap m[2][4];
 };
 
+// Planes of each warpgroup of the two-phase step, balanced by the host.
+struct WgSchedule {
+  int n[4];
+  unsigned char plane[4][MAXPLANES];
+};
+
 // Scalars of one step launch.
 struct StepArgs {
   void* buf[2];         // population buffers (padded planes)
@@ -108,11 +114,14 @@ struct StepLaunch {
   const void* veltab;   // VelTab<C>
   const void* stentab;  // StencilTab<C, P+1>
   const TmaMaps* maps;
+  const WgSchedule* sched;
   int grid;             // CTAs
+  int force_generic;    // 1: single-role kernel instead of the two-phase kernel
   void* stream;
 };
 
-int launch_step_f64(const StepLaunch& L);
+int launch_step_f64_2d(const StepLaunch& L);
+int launch_step_f64_3d(const StepLaunch& L);
 int launch_step_f32(const StepLaunch& L);
 int launch_step_bf16(const StepLaunch& L);
 int launch_step_f16(const StepLaunch& L);
@@ -123,11 +132,13 @@ struct StepInfo {
   int ctas_per_sm;
   size_t smem;
   int bxw, by, bz, tile, tx, ty, tz, vec;
+  int wg;  // warpgroups of the two-phase kernel (0: the single-role kernel runs)
 };
-int step_info_f64(int D, int P, int comp, StepInfo* out);
-int step_info_f32(int D, int P, int comp, StepInfo* out);
-int step_info_bf16(int D, int P, int comp, StepInfo* out);
-int step_info_f16(int D, int P, int comp, StepInfo* out);
+int step_info_f64_2d(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
+int step_info_f64_3d(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
+int step_info_f32(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
+int step_info_bf16(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
+int step_info_f16(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
 
 // Auxiliary kernels (olb_aux.cu).
 struct AuxArgs {

@@ -20,7 +20,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/olb.h"
+#include "olb.h"
 #include "olb_internal.h"
 
 namespace {

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
     _fields_ = [("interp_order", ctypes.c_int), ("storage", ctypes.c_int), ("cs_scale", ctypes.c_double),
                 ("compressible", ctypes.c_int), ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("allow_inexact", ctypes.c_int), ("log_every", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -125,7 +125,7 @@ class Sim:
 
     def __init__(self, shape, dx, velocity_set, hermite_order, tau, dt, interp_order=3, storage="fp64",
                  cs_scale=1.0, compressible=False, gamma=1.4, mu=0.0, rho0=1.0, allow_inexact=False,
-                 log_every=1, stream=None):
+                 log_every=1, kernel="auto", stream=None):
         L = lib()
         g = Grid()
         g.dim = len(shape)
@@ -144,6 +144,7 @@ class Sim:
         o.rho0 = float(rho0)
         o.allow_inexact = int(bool(allow_inexact))
         o.log_every = int(log_every)
+        o.kernel = {"auto": 0, "generic": 1}[kernel]
         if stream is None:
             try:
                 import torch

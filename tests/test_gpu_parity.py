@@ -31,7 +31,7 @@ def olb():
 
 
 def make_pair(olb, name, shape, N=2, p=4, storage="fp64", comp=False, courant=0.4, cs_scale=1.0, tau=0.7,
-              mu=0.02, gamma=1.4, seed=1):
+              mu=0.02, gamma=1.4, seed=1, kernel="auto"):
     vs = V.get(name)
     if cs_scale != 1.0:
         vs = vs.scaled(cs_scale)
@@ -39,7 +39,7 @@ def make_pair(olb, name, shape, N=2, p=4, storage="fp64", comp=False, courant=0.
     dt = courant * dx / np.abs(vs.xi).max()
     prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=tau, compressible=comp, gamma=gamma, mu=mu)
     sim = olb.Sim(shape, dx, name, N, tau, dt, interp_order=p, storage=storage, cs_scale=cs_scale,
-                  compressible=comp, gamma=gamma, mu=mu)
+                  compressible=comp, gamma=gamma, mu=mu, kernel=kernel)
     rng = np.random.default_rng(seed)
     grid = tuple(reversed(shape))
     rho = 1.0 + 0.05 * rng.uniform(-1, 1, grid)
@@ -106,13 +106,31 @@ CASES = [
     ("D3Q27", (40, 20, 18), 2, 4, "bf16", False, 0.4, 1.0),
     ("D3Q27", (40, 20, 18), 2, 4, "fp16", False, 0.4, 1.0),
     ("D3Q27", (37, 20, 18), 2, 4, "fp32", False, 0.4, 1.0),
+    ("D3Q27", (8, 3, 2), 2, 4, "fp32", False, 0.4, 1.0),
+    ("D2Q9", (4, 1), 2, 3, "fp64", False, 0.4, 1 / math.sqrt(3)),
+    ("D3Q45", (64, 40, 24), 2, 4, "fp32", False, 0.4, 1.0),
 ]
 
 
+# the single-role kernel (the automatic choice runs the warp-specialized one
+# for the shifted storages)
+GENERIC = [c for c in CASES if c[4] != "fp64"][:4] + [("D3Q45", (16, 12, 10), 4, 4, "fp32", True, 0.4, 1.0)]
+
+
+@pytest.mark.parametrize("kernel", ["auto"])
 @pytest.mark.parametrize("name,shape,N,p,storage,comp,courant,cs", CASES)
-def test_one_step_parity(olb, name, shape, N, p, storage, comp, courant, cs):
+def test_one_step_parity(olb, name, shape, N, p, storage, comp, courant, cs, kernel):
+    _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel)
+
+
+@pytest.mark.parametrize("name,shape,N,p,storage,comp,courant,cs", GENERIC)
+def test_one_step_parity_generic_kernel(olb, name, shape, N, p, storage, comp, courant, cs):
+    _one_step(olb, name, shape, N, p, storage, comp, courant, cs, "generic")
+
+
+def _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel):
     sim, prm, state = make_pair(olb, name, shape, N=N, p=p, storage=storage, comp=comp, courant=courant,
-                                cs_scale=cs)
+                                cs_scale=cs, kernel=kernel)
     want, diag = oracle_steps(prm, state)
     sim.step(1)
     got = sim.get_populations(np.zeros_like(state))
@@ -134,6 +152,15 @@ def test_interpolation_orders_fp64(olb, p):
     sim.step(1)
     got = sim.get_populations(np.zeros_like(state))
     assert rel_err(got, want, np.zeros(27), "fp64") < 1e-12
+    sim.close()
+
+
+def test_ten_steps_fp32(olb):
+    sim, prm, state = make_pair(olb, "D3Q27", (64, 24, 20), N=2, p=4, storage="fp32")
+    want, _ = oracle_steps(prm, state, steps=10)
+    sim.step(10)
+    got = sim.get_populations(np.zeros_like(state))
+    assert rel_err(got, want, prm.vs.w, "fp32") < 1e-4
     sim.close()
 
 
