@@ -79,18 +79,31 @@ int storage_bytes(int storage) {
   }
 }
 
-int step_info(int D, int P, int storage, int comp, int Q, int force_generic, StepInfo* out) {
+int step_info(int D, int P, int storage, int comp, int Q, int N, int force_generic, StepInfo* out) {
+  const bool d2 = D == 2;
   switch (storage) {
     case OLB_FP64:
-      return D == 2 ? step_info_f64_2d(D, P, comp, Q, force_generic, out)
-                    : step_info_f64_3d(D, P, comp, Q, force_generic, out);
-    case OLB_FP32_SHIFTED: return step_info_f32(D, P, comp, Q, force_generic, out);
-    case OLB_BF16_SHIFTED: return step_info_bf16(D, P, comp, Q, force_generic, out);
-    case OLB_FP16_SHIFTED: return step_info_f16(D, P, comp, Q, force_generic, out);
+      return d2 ? step_info_f64_2d(P, comp, Q, N, force_generic, out) : step_info_f64_3d(P, comp, Q, N, force_generic, out);
+    case OLB_FP32_SHIFTED:
+      return d2 ? step_info_f32_2d(P, comp, Q, N, force_generic, out) : step_info_f32_3d(P, comp, Q, N, force_generic, out);
+    case OLB_BF16_SHIFTED:
+      return d2 ? step_info_bf16_2d(P, comp, Q, N, force_generic, out)
+                : step_info_bf16_3d(P, comp, Q, N, force_generic, out);
+    case OLB_FP16_SHIFTED:
+      return d2 ? step_info_f16_2d(P, comp, Q, N, force_generic, out) : step_info_f16_3d(P, comp, Q, N, force_generic, out);
     default: return -1;
   }
 }
 
+int launch_step(int storage, int D, const StepLaunch& L) {
+  const bool d2 = D == 2;
+  switch (storage) {
+    case OLB_FP64: return d2 ? launch_step_f64_2d(L) : launch_step_f64_3d(L);
+    case OLB_FP32_SHIFTED: return d2 ? launch_step_f32_2d(L) : launch_step_f32_3d(L);
+    case OLB_BF16_SHIFTED: return d2 ? launch_step_bf16_2d(L) : launch_step_bf16_3d(L);
+    default: return d2 ? launch_step_f16_2d(L) : launch_step_f16_3d(L);
+  }
+}
 
 // Lagrange stencil of degree p around offset delta (grid units): first point
 // m0 and weights W[j] = prod_{k != j} (delta - m_k) / (m_j - m_k).
@@ -453,7 +466,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->nnodes = nnodes;
   h->stream = static_cast<cudaStream_t>(opt.stream);
 
-  if (step_info(h->D, h->p, h->storage, h->comp, h->Q, h->force_generic, &h->info) != 0) {
+  if (step_info(h->D, h->p, h->storage, h->comp, h->Q, h->N, h->force_generic, &h->info) != 0) {
     release(h);
     return fail(OLB_EUNSUPPORTED, "interpolation order not built for this storage");
   }
@@ -506,6 +519,15 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   a.inv_cs = 1.0 / cs;
   a.cs2 = cs * cs;
   a.dt = dt;
+  a.f_rho_ref = (float)a.rho_ref;
+  a.f_inv_tau = (float)a.inv_tau;
+  a.f_tau = (float)a.tau;
+  a.f_mu_dt = (float)a.mu_dt;
+  a.f_two_cv = (float)a.two_cv;
+  a.f_gfac = (float)a.gfac;
+  a.f_inv_cs = (float)a.inv_cs;
+  a.f_cs2 = (float)a.cs2;
+  a.f_dt = (float)a.dt;
 
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -661,13 +683,7 @@ int olb_step(olb_handle h, int n) {
     const long long count = h->step_count + 1;
     L.a.src = h->cur;
     L.a.reduce = (count % h->log_every) == 0;
-    int r;
-    switch (h->storage) {
-      case OLB_FP64: r = h->D == 2 ? launch_step_f64_2d(L) : launch_step_f64_3d(L); break;
-      case OLB_FP32_SHIFTED: r = launch_step_f32(L); break;
-      case OLB_BF16_SHIFTED: r = launch_step_bf16(L); break;
-      default: r = launch_step_f16(L); break;
-    }
+    const int r = launch_step(h->storage, h->D, L);
     rc = launch_rc(r, "sl_step");
     if (rc) return rc;
     h->cur ^= 1;

@@ -104,6 +104,9 @@ struct StepArgs {
   double inv_cs;        // 1 / c_s
   double cs2;           // c_s^2
   double dt;
+  // the same scalars rounded to FP32 for the FP32-arithmetic kernels (no
+  // double-to-float conversions on the device)
+  float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt;
 };
 
 // Launch of the fused step for storage `storage` (olb_storage); returns a
@@ -120,11 +123,15 @@ struct StepLaunch {
   void* stream;
 };
 
+// One pair of functions per storage and dimension (olb_step_<storage>_<D>d.cu).
 int launch_step_f64_2d(const StepLaunch& L);
 int launch_step_f64_3d(const StepLaunch& L);
-int launch_step_f32(const StepLaunch& L);
-int launch_step_bf16(const StepLaunch& L);
-int launch_step_f16(const StepLaunch& L);
+int launch_step_f32_2d(const StepLaunch& L);
+int launch_step_f32_3d(const StepLaunch& L);
+int launch_step_bf16_2d(const StepLaunch& L);
+int launch_step_bf16_3d(const StepLaunch& L);
+int launch_step_f16_2d(const StepLaunch& L);
+int launch_step_f16_3d(const StepLaunch& L);
 
 // Shape and occupancy of the step kernel of a configuration: resident CTAs
 // per SM, dynamic shared memory, staged box extents and nodes per tile.
@@ -134,11 +141,14 @@ struct StepInfo {
   int bxw, by, bz, tile, tx, ty, tz, vec;
   int wg;  // warpgroups of the two-phase kernel (0: the single-role kernel runs)
 };
-int step_info_f64_2d(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
-int step_info_f64_3d(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
-int step_info_f32(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
-int step_info_bf16(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
-int step_info_f16(int D, int P, int comp, int Q, int force_generic, StepInfo* out);
+int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_f64_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_f32_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_f32_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_bf16_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_bf16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_f16_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
+int step_info_f16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 
 // Auxiliary kernels (olb_aux.cu).
 struct AuxArgs {

@@ -1,91 +1,138 @@
-// Instantiations of the fused step for double storage.  The two-phase kernel
-// (olb_wg.cuh) is built for p = 3, 4 and runs unless the single-role kernel
-// (olb_step.cuh, built for p = 1, 2, 3, 4, 5, 6) is asked for or is the only one built.
+// Instantiations of the fused step, double storage, D = 2; written by gen_step_instances.py.
 #include "olb_wg.cuh"
 
 namespace olb {
 
-int launch_step_f64_2d(const StepLaunch& L) {
-  using S = double;
-  if (!L.force_generic) {
-    if (L.D == 2 && L.P == 3 && L.compressible == 0) {
-      if (L.a.Q <= 9) return wg::launch_wg<2, 3, S, false, 9>(L);
-      return wg::launch_wg<2, 3, S, false, 27>(L);
-    }
-    if (L.D == 2 && L.P == 3 && L.compressible == 1) {
-      return wg::launch_wg<2, 3, S, true, 27>(L);
-    }
-    if (L.D == 2 && L.P == 4 && L.compressible == 0) {
-      if (L.a.Q <= 9) return wg::launch_wg<2, 4, S, false, 9>(L);
-      return wg::launch_wg<2, 4, S, false, 27>(L);
-    }
-    if (L.D == 2 && L.P == 4 && L.compressible == 1) {
-      return wg::launch_wg<2, 4, S, true, 27>(L);
-    }
+namespace {
+using S = double;
+
+// Two-phase instance for (P, comp, Q, N): its launch and shape, or null.
+using WgLaunch = int (*)(const StepLaunch&);
+using WgOcc = int (*)(size_t*, int*);
+bool pick_wg(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {
+  if (P == 3 && comp == 0 && N == 2 && Q <= 9) {
+    *l = wg::launch_wg<2, 3, S, false, 9, 2>;
+    *o = wg::occupancy_wg<2, 3, S, false, 9, 2>;
+    return true;
   }
-  if (L.D == 2 && L.P == 1 && L.compressible == 0) return launch_one<2, 1, S, false>(L);
-  if (L.D == 2 && L.P == 1 && L.compressible == 1) return launch_one<2, 1, S, true>(L);
-  if (L.D == 2 && L.P == 2 && L.compressible == 0) return launch_one<2, 2, S, false>(L);
-  if (L.D == 2 && L.P == 2 && L.compressible == 1) return launch_one<2, 2, S, true>(L);
-  if (L.D == 2 && L.P == 3 && L.compressible == 0) return launch_one<2, 3, S, false>(L);
-  if (L.D == 2 && L.P == 3 && L.compressible == 1) return launch_one<2, 3, S, true>(L);
-  if (L.D == 2 && L.P == 4 && L.compressible == 0) return launch_one<2, 4, S, false>(L);
-  if (L.D == 2 && L.P == 4 && L.compressible == 1) return launch_one<2, 4, S, true>(L);
-  if (L.D == 2 && L.P == 5 && L.compressible == 0) return launch_one<2, 5, S, false>(L);
-  if (L.D == 2 && L.P == 5 && L.compressible == 1) return launch_one<2, 5, S, true>(L);
-  if (L.D == 2 && L.P == 6 && L.compressible == 0) return launch_one<2, 6, S, false>(L);
-  if (L.D == 2 && L.P == 6 && L.compressible == 1) return launch_one<2, 6, S, true>(L);
+  if (P == 3 && comp == 0 && N == 3 && Q <= 9) {
+    *l = wg::launch_wg<2, 3, S, false, 9, 3>;
+    *o = wg::occupancy_wg<2, 3, S, false, 9, 3>;
+    return true;
+  }
+  if (P == 3 && comp == 0 && N == 2 && true) {
+    *l = wg::launch_wg<2, 3, S, false, 27, 2>;
+    *o = wg::occupancy_wg<2, 3, S, false, 27, 2>;
+    return true;
+  }
+  if (P == 3 && comp == 0 && N == 3 && true) {
+    *l = wg::launch_wg<2, 3, S, false, 27, 3>;
+    *o = wg::occupancy_wg<2, 3, S, false, 27, 3>;
+    return true;
+  }
+  if (P == 3 && comp == 1 && N == 4 && true) {
+    *l = wg::launch_wg<2, 3, S, true, 27, 4>;
+    *o = wg::occupancy_wg<2, 3, S, true, 27, 4>;
+    return true;
+  }
+  if (P == 4 && comp == 0 && N == 2 && Q <= 9) {
+    *l = wg::launch_wg<2, 4, S, false, 9, 2>;
+    *o = wg::occupancy_wg<2, 4, S, false, 9, 2>;
+    return true;
+  }
+  if (P == 4 && comp == 0 && N == 3 && Q <= 9) {
+    *l = wg::launch_wg<2, 4, S, false, 9, 3>;
+    *o = wg::occupancy_wg<2, 4, S, false, 9, 3>;
+    return true;
+  }
+  if (P == 4 && comp == 0 && N == 2 && true) {
+    *l = wg::launch_wg<2, 4, S, false, 27, 2>;
+    *o = wg::occupancy_wg<2, 4, S, false, 27, 2>;
+    return true;
+  }
+  if (P == 4 && comp == 0 && N == 3 && true) {
+    *l = wg::launch_wg<2, 4, S, false, 27, 3>;
+    *o = wg::occupancy_wg<2, 4, S, false, 27, 3>;
+    return true;
+  }
+  if (P == 4 && comp == 1 && N == 4 && true) {
+    *l = wg::launch_wg<2, 4, S, true, 27, 4>;
+    *o = wg::occupancy_wg<2, 4, S, true, 27, 4>;
+    return true;
+  }
+  return false;
+}
+}  // namespace
+
+int launch_step_f64_2d(const StepLaunch& L) {
+  WgLaunch l;
+  WgOcc o;
+  if (!L.force_generic && pick_wg(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);
+  if (L.P == 1 && L.compressible == 0) return launch_one<2, 1, S, false>(L);
+  if (L.P == 1 && L.compressible == 1) return launch_one<2, 1, S, true>(L);
+  if (L.P == 2 && L.compressible == 0) return launch_one<2, 2, S, false>(L);
+  if (L.P == 2 && L.compressible == 1) return launch_one<2, 2, S, true>(L);
+  if (L.P == 3 && L.compressible == 0) return launch_one<2, 3, S, false>(L);
+  if (L.P == 3 && L.compressible == 1) return launch_one<2, 3, S, true>(L);
+  if (L.P == 4 && L.compressible == 0) return launch_one<2, 4, S, false>(L);
+  if (L.P == 4 && L.compressible == 1) return launch_one<2, 4, S, true>(L);
+  if (L.P == 5 && L.compressible == 0) return launch_one<2, 5, S, false>(L);
+  if (L.P == 5 && L.compressible == 1) return launch_one<2, 5, S, true>(L);
+  if (L.P == 6 && L.compressible == 0) return launch_one<2, 6, S, false>(L);
+  if (L.P == 6 && L.compressible == 1) return launch_one<2, 6, S, true>(L);
   return -1;
 }
 
-int step_info_f64_2d(int D, int P, int comp, int Q, int force_generic, StepInfo* out) {
-  using S = double;
-  if (D == 2 && P == 1) {
+int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out) {
+  WgLaunch l;
+  WgOcc o;
+  out->wg = 0;
+  if (P == 1) {
     layout_of<2, 1, S>(out);
-    out->wg = 0;
-    out->ctas_per_sm = comp ? occupancy_one<2, 1, S, true>(&out->smem) : occupancy_one<2, 1, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 1, S, true>(&out->smem)
+                            : occupancy_one<2, 1, S, false>(&out->smem);
     return 0;
   }
-  if (D == 2 && P == 2) {
+  if (P == 2) {
     layout_of<2, 2, S>(out);
-    out->wg = 0;
-    out->ctas_per_sm = comp ? occupancy_one<2, 2, S, true>(&out->smem) : occupancy_one<2, 2, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 2, S, true>(&out->smem)
+                            : occupancy_one<2, 2, S, false>(&out->smem);
     return 0;
   }
-  if (D == 2 && P == 3) {
+  if (P == 3) {
     layout_of<2, 3, S>(out);
-    out->wg = 0;
-    if (!force_generic) {
+    if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
       int nwg = 0;
-      out->ctas_per_sm = comp ? wg::occupancy_wg<2, 3, S, true, 27>(&out->smem, &nwg) : (Q <= 9 ? wg::occupancy_wg<2, 3, S, false, 9>(&out->smem, &nwg) : wg::occupancy_wg<2, 3, S, false, 27>(&out->smem, &nwg));
+      out->ctas_per_sm = o(&out->smem, &nwg);
       out->wg = nwg;
       return 0;
     }
-    out->ctas_per_sm = comp ? occupancy_one<2, 3, S, true>(&out->smem) : occupancy_one<2, 3, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 3, S, true>(&out->smem)
+                            : occupancy_one<2, 3, S, false>(&out->smem);
     return 0;
   }
-  if (D == 2 && P == 4) {
+  if (P == 4) {
     layout_of<2, 4, S>(out);
-    out->wg = 0;
-    if (!force_generic) {
+    if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
       int nwg = 0;
-      out->ctas_per_sm = comp ? wg::occupancy_wg<2, 4, S, true, 27>(&out->smem, &nwg) : (Q <= 9 ? wg::occupancy_wg<2, 4, S, false, 9>(&out->smem, &nwg) : wg::occupancy_wg<2, 4, S, false, 27>(&out->smem, &nwg));
+      out->ctas_per_sm = o(&out->smem, &nwg);
       out->wg = nwg;
       return 0;
     }
-    out->ctas_per_sm = comp ? occupancy_one<2, 4, S, true>(&out->smem) : occupancy_one<2, 4, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 4, S, true>(&out->smem)
+                            : occupancy_one<2, 4, S, false>(&out->smem);
     return 0;
   }
-  if (D == 2 && P == 5) {
+  if (P == 5) {
     layout_of<2, 5, S>(out);
-    out->wg = 0;
-    out->ctas_per_sm = comp ? occupancy_one<2, 5, S, true>(&out->smem) : occupancy_one<2, 5, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 5, S, true>(&out->smem)
+                            : occupancy_one<2, 5, S, false>(&out->smem);
     return 0;
   }
-  if (D == 2 && P == 6) {
+  if (P == 6) {
     layout_of<2, 6, S>(out);
-    out->wg = 0;
-    out->ctas_per_sm = comp ? occupancy_one<2, 6, S, true>(&out->smem) : occupancy_one<2, 6, S, false>(&out->smem);
+    out->ctas_per_sm = comp ? occupancy_one<2, 6, S, true>(&out->smem)
+                            : occupancy_one<2, 6, S, false>(&out->smem);
     return 0;
   }
   return -1;

@@ -9,21 +9,24 @@
 //   Each warpgroup owns a host-balanced list of planes and streams them
 //   through its own shared-memory box (one TMA copy per plane, completion on
 //   the warpgroup's mbarrier; L2 prefetch of the plane after next), its own
-//   z -> y -> x passes (warpgroup-local named barriers only) and writes the
-//   pulled values f~_i of the tile to the CTA's staging slab (kept in L2).
-//   No per-node state is carried from plane to plane, so the warpgroups never
-//   wait for each other inside the phase.
+//   z -> y -> x passes (warpgroup-local named barriers only; the z and y
+//   passes use paired FP32 FMAs) and writes the pulled values f~_i of the
+//   tile to the CTA's staging slab (kept in L2).  No per-node state is carried
+//   from plane to plane, so the warpgroups never wait for each other here.
 //
-//   Phase B (collide).  One thread per node loads the Q pulled values of its
-//   node (all loads in flight together), forms rho, rho u (and the
-//   temperature), the equilibrium and the BGK update with the velocity loop
-//   unrolled (QM >= Q slots, so the per-velocity constants are constant-bank
-//   operands), and writes the new state and its periodic copies.
+//   Phase B (collide).  One thread per node loads its Q pulled values (all
+//   loads in flight together), forms rho, rho u (and the temperature), the
+//   order-N equilibrium and the BGK update with the velocity loop unrolled
+//   (per-velocity constants are constant-bank operands), and stores the new
+//   state together with its periodic copies in the ghost layers (offsets
+//   computed once per node).
 //
 // Two CTA barriers per tile separate the phases.  Every mbarrier wait is
 // bounded: a wait that runs out raises the device error flag and the kernel
 // returns after its copies in flight have landed.
 #pragma once
+
+#include <type_traits>
 
 #include "olb_step.cuh"
 
@@ -52,6 +55,58 @@ struct GLayout {
   static_assert(NWG >= 1, "one warpgroup must fit");
 };
 
+// Scalars of the step in the arithmetic type.
+template <typename C>
+struct Scal;
+template <>
+struct Scal<float> {
+  float rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt;
+  __device__ __forceinline__ explicit Scal(const StepArgs& a)
+      : rho_ref(a.f_rho_ref), inv_tau(a.f_inv_tau), tau(a.f_tau), mu_dt(a.f_mu_dt), two_cv(a.f_two_cv),
+        gfac(a.f_gfac), inv_cs(a.f_inv_cs), cs2(a.f_cs2), dt(a.f_dt) {}
+};
+template <>
+struct Scal<double> {
+  double rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt;
+  __device__ __forceinline__ explicit Scal(const StepArgs& a)
+      : rho_ref(a.rho_ref), inv_tau(a.inv_tau), tau(a.tau), mu_dt(a.mu_dt), two_cv(a.two_cv), gfac(a.gfac),
+        inv_cs(a.inv_cs), cs2(a.cs2), dt(a.dt) {}
+};
+
+// Two values of the arithmetic type; FP32 pairs use the paired FMA.
+template <typename C>
+struct Pr;
+template <>
+struct Pr<float> {
+  using T = float2;
+  static __device__ __forceinline__ T set(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ T mul(T a, T b) { return __fmul2_rn(a, b); }
+};
+template <>
+struct Pr<double> {
+  using T = double2;
+  static __device__ __forceinline__ T set(double a) { return make_double2(a, a); }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+  static __device__ __forceinline__ T mul(T a, T b) { return make_double2(a.x * b.x, a.y * b.y); }
+};
+
+// A 4-node x group as two pairs.
+template <typename SRC, typename T>
+__device__ __forceinline__ void ld4p(const SRC* p, T& lo, T& hi) {
+  typename Store<SRC>::C v[4];
+  ld4(p, v);
+  lo.x = v[0];
+  lo.y = v[1];
+  hi.x = v[2];
+  hi.y = v[3];
+}
+template <typename C, typename T>
+__device__ __forceinline__ void st4p(C* p, T lo, T hi) {
+  const C v[4] = {lo.x, lo.y, hi.x, hi.y};
+  st4(p, v);
+}
+
 __device__ __forceinline__ void wg_barrier(int wg) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(1 + wg), "r"(WGT) : "memory");
 }
@@ -69,20 +124,46 @@ __device__ __forceinline__ bool wg_any(int wg, bool c) {
 }
 
 // Offset of the single periodic copy of coordinate c in the ghost layers of an
-// axis with n >= gl + gr nodes (0 when c has none).
-__device__ __forceinline__ int one_image(int c, int n, int gl, int gr) {
-  if (c < gr) return n;
-  if (c >= n - gl) return -n;
+// axis with n >= gl + gr nodes (0 when c has none); only copies the stencil
+// reaches are written.
+__device__ __forceinline__ int one_image(int c, int n, int reach_lo, int reach_hi) {
+  if (c < reach_hi) return n;
+  if (c >= n - reach_lo) return -n;
   return 0;
 }
 
-template <int D, int P, typename S, bool COMP, int QM>
+// Equilibrium of order N (Appendix A) in closed form, f^eq_i/(w_i rho) - 1.
+template <typename C, bool COMP, int N>
+__device__ __forceinline__ C phi_n(C s, C q, C t, C rD, C rpoly) {
+  const C s2 = s * s;
+  C v = s;
+  {
+    C h = s2 - q;
+    if (COMP) h = fma(t, rD, h);
+    v = fma(C(0.5), h, v);
+  }
+  if (N >= 3) {
+    C h = s * (s2 - C(3) * q);
+    if (COMP) h = fma(C(3) * t * s, rD - C(2), h);
+    v = fma(C(1.0 / 6.0), h, v);
+  }
+  if (N >= 4) {
+    C h = s2 * s2 - C(6) * s2 * q + C(3) * q * q;
+    if (COMP) h += C(6) * t * (s2 * (rD - C(4)) - q * (rD - C(2))) + C(3) * t * t * rpoly;
+    v = fma(C(1.0 / 24.0), h, v);
+  }
+  return v;
+}
+
+template <int D, int P, typename S, bool COMP, int QM, int N>
 __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
     sl_wg_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
                  const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
                  const __grid_constant__ TmaMaps maps, const __grid_constant__ WgSchedule sched) {
   using L = GLayout<D, P, S>;
   using C = typename Store<S>::C;
+  using PR = Pr<C>;
+  using T2 = typename PR::T;
   constexpr int NT = L::NT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
@@ -97,11 +178,12 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
 
   const int Q = a.Q, planes = a.planes;
   const Padded& pd = a.pad;
+  const Scal<C> sc(a);
   const CUtensorMap* maps4 = maps.m[a.src];
   const int nplan = sched.n[wg];
   S* __restrict__ dst = static_cast<S*>(a.buf[a.src ^ 1]);
   C* __restrict__ scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE;
-  const unsigned long long keep = policy_evict_last(), stream_out = policy_evict_first();
+  const unsigned long long keep = policy_evict_last();
 
   auto box_coords = [&](int tile, int plane, int& X, int& Y, int& Z) {
     const int tx = tile % a.nt[0], r = tile / a.nt[0];
@@ -142,6 +224,11 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
   unsigned parity = 0;
   bool failed = false;
 
+  // every axis holds at least one stencil reach on each side: a node has at
+  // most one periodic copy per axis
+  const bool simple = a.quad_ok && pd.n[0] >= pd.gl[0] + pd.gr[0] && pd.n[1] >= pd.gl[1] + pd.gr[1] &&
+                      pd.n[2] >= pd.gl[2] + pd.gr[2];
+
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     // ---------------- phase A: pull every plane of the tile -----------------
     for (int k = 0; k < nplan && !failed; ++k) {
@@ -164,63 +251,63 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       }
       const C* xsrc_c = nullptr;
       if (zact) {
-        C W[P + 1];
+        T2 W[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) W[j] = st.W[i][2][j];
+        for (int j = 0; j <= P; ++j) W[j] = PR::set(st.W[i][2][j]);
         const int BYA = yact ? L::BY : L::TY;
         const int items = L::NQX * BYA * (L::TZ / L::ZCH);
         const int PLs = BYA * L::BXW;
         for (int item = wt; item < items; item += WGT) {
           const int q = item % L::NQX, r = item / L::NQX, y = r % BYA, zc = r / BYA;
           const int off = (zc * L::ZCH * BYA + y) * L::BXW + 4 * q;
-          C v[L::ZCH + P][4];
+          T2 v[L::ZCH + P][2];
 #pragma unroll
-          for (int kk = 0; kk < L::ZCH + P; ++kk) ld4(box + off + kk * PLs, v[kk]);
+          for (int kk = 0; kk < L::ZCH + P; ++kk) ld4p(box + off + kk * PLs, v[kk][0], v[kk][1]);
 #pragma unroll
           for (int z = 0; z < L::ZCH; ++z) {
-            C o[4];
+            T2 o[2];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              C acc = W[0] * v[z][e];
+            for (int h = 0; h < 2; ++h) {
+              T2 acc = PR::mul(W[0], v[z][h]);
 #pragma unroll
-              for (int kk = 1; kk <= P; ++kk) acc = fma(W[kk], v[z + kk][e], acc);
-              o[e] = acc;
+              for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], v[z + kk][h], acc);
+              o[h] = acc;
             }
-            st4(bufA + off + z * PLs, o);
+            st4p(bufA + off + z * PLs, o[0], o[1]);
           }
         }
         wg_barrier(wg);
         xsrc_c = bufA;
       }
       if (yact) {
-        C W[P + 1];
+        T2 W[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) W[j] = st.W[i][1][j];
+        for (int j = 0; j <= P; ++j) W[j] = PR::set(st.W[i][1][j]);
         constexpr int NYC = L::TY / L::YCH;
         constexpr int items = L::NQX * L::TZ * NYC;
         for (int item = wt; item < items; item += WGT) {
           const int q = item % L::NQX, r = item / L::NQX, yc = r % NYC, z = r / NYC;
           const int off = (z * L::BY + yc * L::YCH) * L::BXW + 4 * q;
-          C v[L::YCH + P][4];
+          T2 v[L::YCH + P][2];
           if (zact) {
 #pragma unroll
-            for (int kk = 0; kk < L::YCH + P; ++kk) ld4(bufA + off + kk * L::BXW, v[kk]);
+            for (int kk = 0; kk < L::YCH + P; ++kk) ld4p(bufA + off + kk * L::BXW, v[kk][0], v[kk][1]);
           } else {
 #pragma unroll
-            for (int kk = 0; kk < L::YCH + P; ++kk) ld4(box + off + kk * L::BXW, v[kk]);
+            for (int kk = 0; kk < L::YCH + P; ++kk) ld4p(box + off + kk * L::BXW, v[kk][0], v[kk][1]);
           }
           C* o = bufB + (z * L::TY + yc * L::YCH) * L::BXW + 4 * q;
 #pragma unroll
           for (int y = 0; y < L::YCH; ++y) {
-            C w4[4];
+            T2 w2[2];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              C acc = W[0] * v[y][e];
+            for (int h = 0; h < 2; ++h) {
+              T2 acc = PR::mul(W[0], v[y][h]);
 #pragma unroll
-              for (int kk = 1; kk <= P; ++kk) acc = fma(W[kk], v[y + kk][e], acc);
-              w4[e] = acc;
+              for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], v[y + kk][h], acc);
+              w2[h] = acc;
             }
-            st4(o + y * L::BXW, w4);
+            st4p(o + y * L::BXW, w2[0], w2[1]);
           }
         }
         wg_barrier(wg);
@@ -262,15 +349,15 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
     const int tx = tile % a.nt[0], tr = tile / a.nt[0];
     const int ty = tr % a.nt[1], tz = tr / a.nt[1];
     const bool red = a.reduce != 0;
-    const bool simple = a.quad_ok && pd.n[0] >= pd.gl[0] + pd.gr[0] && pd.n[1] >= pd.gl[1] + pd.gr[1] &&
-                        pd.n[2] >= pd.gl[2] + pd.gr[2];
     C tsum[NRED];
 #pragma unroll
     for (int c = 0; c < NRED; ++c) tsum[c] = C(0);
-    for (int n = tid; n < L::TILE; n += NT) {
+
+    auto collide = [&](int n, auto RED) {
+      constexpr bool R = decltype(RED)::value;
       const int lx = n % L::TX, ly = (n / L::TX) % L::TY, lz = n / (L::TX * L::TY);
       const int x = tx * L::TX + lx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
-      const bool inside = x < pd.n[0] && y < pd.n[1] && z < pd.n[2];
+      if (x >= pd.n[0] || y >= pd.n[1] || z >= pd.n[2]) return;
       C f[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) f[i] = i < Q ? scr[(size_t)i * L::TILE + n] : C(0);
@@ -292,12 +379,11 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
           }
         }
       }
-      const C rho = C(a.rho_ref) + A;
+      const C rho = sc.rho_ref + A;
       const C ir = C(1) / rho;
-      const C ics = C(a.inv_cs);
-      const C uhx = jx * ir * ics, uhy = jy * ir * ics, uhz = jz * ir * ics;
+      const C uhx = jx * ir * sc.inv_cs, uhy = jy * ir * sc.inv_cs, uhz = jz * ir * sc.inv_cs;
       const C q = uhx * uhx + uhy * uhy + uhz * uhz;
-      C itau = C(a.inv_tau), tt = C(0), gA = C(0), rth = C(0), theta = C(1), tau = C(a.tau);
+      C itau = sc.inv_tau, tt = C(0), gA = C(0), rth = C(0), theta = C(1), tau = sc.tau;
       if (COMP) {
         Bd += (double)Bp;
         // sum of the pulled g (Sec. 3 temperature relation), FP32 groups into FP64
@@ -315,63 +401,90 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
         Gd += (double)Gp;
         const double r = (double)rho;
         const double jj = (double)jx * jx + (double)jy * jy + (double)jz * jz;
-        const double X = Bd + Gd - jj / r - a.two_cv * (double)A;
-        tt = C(X) / (C(a.two_cv) * rho);
+        const double X = Bd + Gd - jj / r - (double)sc.two_cv * (double)A;
+        tt = C(X) / (sc.two_cv * rho);
         theta = C(1) + tt;
-        tau = C(a.mu_dt) / (rho * theta) + C(0.5);
+        tau = sc.mu_dt / (rho * theta) + C(0.5);
         itau = C(1) / tau;
         gA = fma(rho, tt, A);
         rth = rho * theta;
       }
-      // equilibrium (Appendix A), BGK (Sec. 3), stores with the periodic copies
-      const long long off = pad_index(pd, x, y, z);
+      // periodic copies of this node in the ghost layers: 0, 1, 3 or 7 of them
       const int dx = one_image(x, pd.n[0], pd.gl[0], pd.gr[0]);
       const int dy = one_image(y, pd.n[1], pd.gl[1], pd.gr[1]);
       const int dz = D == 3 ? one_image(z, pd.n[2], pd.gl[2], pd.gr[2]) : 0;
-      const bool any_img = dx != 0 || dy != 0 || dz != 0;
-      const long long sx = dx, sy = (long long)dy * pd.np[0], sz = (long long)dz * pd.np[0] * pd.np[1];
+      const int sx = dx, sy = dy * pd.np[0], sz = dz * pd.np[0] * pd.np[1];
+      // image offsets: the single-axis ones, then the pairs, then the corner
+      const int nax = (sx != 0) + (sy != 0) + (sz != 0);
+      const int nimg = nax == 0 ? 0 : (nax == 1 ? 1 : (nax == 2 ? 3 : 7));
+      const int a0 = sx ? sx : (sy ? sy : sz);
+      const int a1 = sx ? (sy ? sy : sz) : (sy ? sz : 0);
+      const int i0 = a0, i1 = a1, i2 = nax == 3 ? sz : a0 + a1;
+      const int i3 = sx + sy, i4 = sx + sz, i5 = sy + sz, i6 = sx + sy + sz;
+      const bool many = !simple && nimg > 0;  // tiny grid: several copies per axis
+      // equilibrium (Appendix A), BGK (Sec. 3) and the stores
+      S* pf = dst + pad_index(pd, x, y, z);
       C Pi[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
-        const C s = fma(vt.xih[i][0], uhx, fma(vt.xih[i][1], uhy, D == 3 ? vt.xih[i][2] * uhz : C(0)));
-        const C ph = phi_m1<C, COMP>(s, q, tt, vt.rD[i], vt.rpoly[i], a.N);
+        C s = vt.xih[i][0] * uhx;
+        s = fma(vt.xih[i][1], uhy, s);
+        if (D == 3) s = fma(vt.xih[i][2], uhz, s);
+        const C ph = phi_n<C, COMP, N>(s, q, tt, vt.rD[i], vt.rpoly[i]);
         const C feqd = vt.w[i] * fma(rho, ph, A);
         const C fneq = f[i] - feqd;
         const S o = Store<S>::st(fma(-fneq, itau, f[i]));
-        S og{};
+        pf[0] = o;
         if (COMP) {
           const C gv = scr[(size_t)(Q + i) * L::TILE + n];
-          const C geqd = vt.w[i] * C(a.gfac) * fma(rth, ph, gA);
-          og = Store<S>::st(fma(-(gv - geqd), itau, gv));
-        }
-        if (inside) {
-          S* pf = dst + (long long)i * pd.plane;
-          S* pg = dst + (long long)(Q + i) * pd.plane;
-          pf[off] = o;
-          if (COMP) pg[off] = og;
-          if (any_img) {
-            if (simple) {
-#pragma unroll
-              for (int c = 1; c < 8; ++c) {
-                if (((c & 1) && !dx) || ((c & 2) && !dy) || ((c & 4) && !dz)) continue;
-                const long long o2 = off + ((c & 1) ? sx : 0) + ((c & 2) ? sy : 0) + ((c & 4) ? sz : 0);
-                pf[o2] = o;
-                if (COMP) pg[o2] = og;
-              }
+          const C geqd = vt.w[i] * sc.gfac * fma(rth, ph, gA);
+          const S og = Store<S>::st(fma(-(gv - geqd), itau, gv));
+          S* pg = pf + (long long)Q * pd.plane;
+          pg[0] = og;
+          if (nimg) {
+            if (many) {
+              store_all_images(pg - pad_index(pd, x, y, z), pd, x, y, z, og);
             } else {
-              store_all_images(pf, pd, x, y, z, o);
-              if (COMP) store_all_images(pg, pd, x, y, z, og);
+              pg[i0] = og;
+              if (nimg > 1) {
+                pg[i1] = og;
+                pg[i2] = og;
+                if (nimg > 3) {
+                  pg[i3] = og;
+                  pg[i4] = og;
+                  pg[i5] = og;
+                  pg[i6] = og;
+                }
+              }
             }
           }
         }
-        if (red) {
+        if (nimg) {
+          if (many) {
+            store_all_images(pf - pad_index(pd, x, y, z), pd, x, y, z, o);
+          } else {
+            pf[i0] = o;
+            if (nimg > 1) {
+              pf[i1] = o;
+              pf[i2] = o;
+              if (nimg > 3) {
+                pf[i3] = o;
+                pf[i4] = o;
+                pf[i5] = o;
+                pf[i6] = o;
+              }
+            }
+          }
+        }
+        pf += pd.plane;
+        if (R) {
 #pragma unroll
           for (int c = 0; c < 6; ++c) Pi[c] = fma(vt.xx[i][c], fneq, Pi[c]);
         }
       }
-      if (red && inside) {
-        const C u2 = q * C(a.cs2);
+      if (R) {
+        const C u2 = q * sc.cs2;
         tsum[0] += C(0.5) * u2;
         tsum[1] += C(0.5) * rho * u2;
         tsum[3] += A;
@@ -380,13 +493,20 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
         tsum[6] += jz;
         const bool fin = isfinite(rho) && isfinite(uhx) && isfinite(uhy) && isfinite(uhz) && isfinite(theta);
         tsum[7] += fin ? C(0) : C(1);
-        const C pres = rho * theta * C(a.cs2);
-        const C den = C(2) * pres * tau * C(a.dt);
-        const C ss = (Pi[0] * Pi[0] + Pi[1] * Pi[1] + Pi[2] * Pi[2] + C(2) * (Pi[3] * Pi[3] + Pi[4] * Pi[4] + Pi[5] * Pi[5])) /
+        const C pres = rho * theta * sc.cs2;
+        const C den = C(2) * pres * tau * sc.dt;
+        const C ss = (Pi[0] * Pi[0] + Pi[1] * Pi[1] + Pi[2] * Pi[2] +
+                      C(2) * (Pi[3] * Pi[3] + Pi[4] * Pi[4] + Pi[5] * Pi[5])) /
                      (den * den);
-        const C nu = C(a.cs2) * theta * C(a.dt) * (tau - C(0.5));
+        const C nu = sc.cs2 * theta * sc.dt * (tau - C(0.5));
         tsum[2] += C(2) * nu * ss;
       }
+    };
+
+    if (red) {
+      for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, true>());
+    } else {
+      for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, false>());
     }
     if (red) {
 #pragma unroll
@@ -415,11 +535,11 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
   }
 }
 
-template <int D, int P, typename S, bool COMP, int QM>
+template <int D, int P, typename S, bool COMP, int QM, int N>
 int launch_wg(const StepLaunch& Lc) {
   using C = typename Store<S>::C;
   using Lay = GLayout<D, P, S>;
-  auto kern = sl_wg_kernel<D, P, S, COMP, QM>;
+  auto kern = sl_wg_kernel<D, P, S, COMP, QM, N>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES);
@@ -432,10 +552,10 @@ int launch_wg(const StepLaunch& Lc) {
   return (int)cudaGetLastError();
 }
 
-template <int D, int P, typename S, bool COMP, int QM>
+template <int D, int P, typename S, bool COMP, int QM, int N>
 int occupancy_wg(size_t* smem, int* nwg) {
   using Lay = GLayout<D, P, S>;
-  auto kern = sl_wg_kernel<D, P, S, COMP, QM>;
+  auto kern = sl_wg_kernel<D, P, S, COMP, QM, N>;
   *smem = Lay::BYTES;
   *nwg = Lay::NWG;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES) != cudaSuccess)
