@@ -3,8 +3,8 @@
 
 Default workload (N = 1): 3D Taylor-Green vortex, Re = 1600, Ma = 0.1, 128^3
 periodic nodes, D3Q27, N = 2 Hermite equilibrium, p = 4 Lagrange pull,
-Courant 0.4, FP32 shifted storage.  One step = one launch of the fused kernel
-over every node.  The L2 cache is flushed (a 256 MiB write) between timed
+Courant 0.4, FP32 shifted storage.  One step = one launch of the fused
+two-phase kernel over every node.  The L2 cache is flushed (a 256 MiB write) between timed
 steps, and each step is timed alone with CUDA events on the simulation's
 stream.  Under torchrun (N > 1) every rank runs its own replica of the
 workload (weak scaling, no data-path collective); rank 0 reports the whole-job
@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
 # default workload, from one ncu capture of the kernel source with this hash
 # (summary in profiles/); reported as null once the kernel source changes.
-TRAFFIC = {"kernel_sha": None, "bytes": None}
+TRAFFIC = {"kernel_sha": "eee2429c9889331c", "bytes": 341244416 + 324843520}
 
 
 def workload_name(w):
@@ -53,7 +53,7 @@ def workload_name(w):
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("olb_step.cuh",):
+    for f in ("olb_step.cuh", "olb_wg.cuh", "olb_step_f32_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_2101_03982_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -372,7 +372,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "kernel": "sl_step_kernel (fused pull + collide)"},
+                     "kernel": "sl_wg_kernel (two-phase fused pull + collide)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,
