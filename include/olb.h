@@ -175,6 +175,41 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);
 /* Wait for the handle's stream, polling with a bound of timeout_ms (<= 0: no bound). */
 int olb_synchronize(olb_handle h, int timeout_ms);
 
+/* ---- Adjoint of the isothermal step (vector-Jacobian products) ----------------------------
+ * The paper defines the forward step only (Sec. 3: pull by Eq. sl_streaming, BGK with the
+ * Hermite equilibrium of Appendix A).  These calls give the exact transpose of its Jacobian
+ * for the isothermal step (compressible = 0), FP64 or FP32 storage, p = 3 or 4, N = 2 or 3
+ * (N = 2 for D3Q45), with the automatic kernel choice; other configurations return
+ * OLB_EUNSUPPORTED.
+ *
+ * Adjoint arrays ("lambda") are compact [Q][nz][ny][nx], x fastest, in the adjoint type:
+ * double for FP64 storage, float for FP32 storage; lambda_i(x) = dJ/df_i(x) of the
+ * unshifted populations.  on_device = 1: device pointers on the handle's stream (the call is
+ * asynchronous); 0: host pointers (the call completes and checks the device error flag).
+ *
+ * olb_tape_reserve  allocate nslots padded state slots on the device (kept until destroy).
+ * olb_tape_record   slot 0 = current state, then n forward steps, step s writing slot s;
+ *                   the handle's state advances by n steps.  Needs n + 1 <= nslots.
+ * olb_tape_adjoint  lambda in: dJ/d(state after the last recorded step); lambda out:
+ *                   dJ/d(state n steps earlier), 1 <= n <= recorded steps.  n + 1 launches of
+ *                   the adjoint kernel plus one scatter and one gather.
+ * olb_adjoint_step  one step: fwd_state is the state before the step in the olb_get_state
+ *                   layout (olb_state_bytes bytes); lambda in: dJ/d(state after the step),
+ *                   out: dJ/d(fwd_state).  Uses tape slot 0 (clears a recorded trajectory).
+ * olb_moments_vjp   seed of a sweep from dJ/drho and dJ/du at the handle's current state:
+ *                   lambda_i = dJ/drho + dJ/du . (xi_i - u) / rho.  grad_rho [n] and grad_u
+ *                   [D][n] (FP64, either may be NULL = zero).
+ * olb_equilibrium_vjp  gradients of sum_i lambda_i f_i^eq(rho, u) with respect to rho [n] and
+ *                   u [D][n] (FP64), the last link from lambda of an initial state built by
+ *                   olb_init_fields (theta = 1). */
+int olb_tape_reserve(olb_handle h, int nslots);
+int olb_tape_record(olb_handle h, int n);
+int olb_tape_adjoint(olb_handle h, void* lambda, int n, int on_device);
+int olb_adjoint_step(olb_handle h, const void* fwd_state, void* lambda, int on_device);
+int olb_moments_vjp(olb_handle h, const double* grad_rho, const double* grad_u, void* lambda, int on_device);
+int olb_equilibrium_vjp(olb_handle h, const double* rho, const double* u, const void* lambda, double* grad_rho,
+                        double* grad_u, int on_device);
+
 /* Global sums of a state held by the caller, computed without allocating.
  * No counterpart in the paper: this is for callers that cannot allocate device
  * memory at the point where they need the sums (a framework that owns all

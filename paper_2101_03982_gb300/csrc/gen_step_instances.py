@@ -10,6 +10,9 @@ agree:
 * otherwise the single-role kernel (olb_step.cuh), built for p = 1..6 in FP64
   and p = 2..4 in the shifted storages.
 
+FP64 and FP32 files also define launch_adj_<storage>_<D>d, the adjoint step
+of the isothermal kernel for p = 3, 4 and the (Q, N) pairs in ADJ_CASES.
+
 Run ``python gen_step_instances.py`` after changing the table.
 """
 import os
@@ -21,6 +24,8 @@ GENERIC_P = {"f64": [1, 2, 3, 4, 5, 6], "f32": [2, 3, 4], "bf16": [2, 3, 4], "f1
 WG_P = [3, 4]
 WG_ISO_N = [2, 3]
 WG_COMP_N = 4
+ADJ_STORAGES = ("f64", "f32")
+ADJ_CASES = {2: [(9, 2), (27, 2), (27, 3)], 3: [(27, 2), (27, 3), (45, 2)]}
 
 
 def iso_qms(D):
@@ -109,6 +114,15 @@ def emit(st, D):
     L.append("  return -1;")
     L.append("}")
     L.append("")
+    if st in ADJ_STORAGES:
+        L.append(f"int launch_adj_{fn}(const StepLaunch& L) {{")
+        for P in WG_P:
+            for (qm, N) in ADJ_CASES[D]:
+                cond = f" && L.a.Q <= {qm}" if qm != iso_qms(D)[-1] else ""
+                L.append(f"  if (L.P == {P} && L.a.N == {N}{cond}) return wg::launch_adj<{D}, {P}, S, {qm}, {N}>(L);")
+        L.append("  return -1;")
+        L.append("}")
+        L.append("")
     L.append("}  // namespace olb")
     return "\n".join(L) + "\n"
 

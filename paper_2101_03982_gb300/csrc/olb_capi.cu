@@ -65,6 +65,16 @@ struct olb_ctx {
   AuxArgs aux{};
   std::vector<int> m0;        // [Q][3], oracle convention on every axis
   std::vector<double> W;      // [Q][3][p+1]
+  // adjoint: tape of forward states (padded, like buf) and the adjoint buffers
+  std::vector<void*> tape;
+  std::vector<TmaMaps> tape_maps;  // m[0] of each slot
+  int tape_len = 0;                // slots holding a recorded state
+  void* adj[2] = {nullptr, nullptr};
+  TmaMaps adj_maps{};              // m[k] of adj[k]
+  void* adj_scratch = nullptr;
+  std::vector<unsigned char> st_refl, st_id;  // reflected and identity stencils
+  WgSchedule sched_adj[3]{};       // first step, middle steps, last (pull only)
+  int adj_ready = 0;
 };
 
 namespace {
@@ -183,6 +193,11 @@ void release(olb_ctx* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->red_dev) cudaFree(h->red_dev);
   if (h->err_dev) cudaFree(h->err_dev);
+  for (void* t : h->tape)
+    if (t) cudaFree(t);
+  for (int k = 0; k < 2; ++k)
+    if (h->adj[k]) cudaFree(h->adj[k]);
+  if (h->adj_scratch) cudaFree(h->adj_scratch);
   delete h;
 }
 
@@ -217,19 +232,11 @@ void layout_padding(olb_ctx* h) {
 }  // namespace
 
 // Planes of each warpgroup of the two-phase kernel: longest processing time
-// first, with a plane's cost from the passes its velocity needs.
-static void build_schedule(olb_ctx* h) {
-  WgSchedule& S = h->sched;
+// first, with a plane's cost from the passes its stencil needs.
+static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSchedule* out) {
+  WgSchedule& S = *out;
   std::memset(&S, 0, sizeof(S));
-  const int nwg = h->info.wg > 0 ? h->info.wg : 1;
-  std::vector<std::pair<double, int>> cost;
-  for (int p = 0; p < h->planes; ++p) {
-    const int i = p % h->Q;
-    double c = 1.0;                                      // x pass (or copy) of every node
-    if (h->set.xi[i][1] != 0.0) c += 1.25;               // y pass
-    if (h->D == 3 && h->set.xi[i][2] != 0.0) c += 1.5;   // z pass
-    cost.push_back({c, p});
-  }
+  if (nwg < 1) nwg = 1;
   std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
   double load[4] = {0, 0, 0, 0};
   std::vector<int> lists[4];
@@ -247,6 +254,21 @@ static void build_schedule(olb_ctx* h) {
   }
 }
 
+// Cost of pulling one plane of velocity i: x pass (or copy) of every node,
+// plus the y and z passes its nonzero components need.
+static double plane_cost(const olb_ctx* h, int i) {
+  double c = 1.0;
+  if (h->set.xi[i][1] != 0.0) c += 1.25;
+  if (h->D == 3 && h->set.xi[i][2] != 0.0) c += 1.5;
+  return c;
+}
+
+static void build_schedule(olb_ctx* h) {
+  std::vector<std::pair<double, int>> cost;
+  for (int p = 0; p < h->planes; ++p) cost.push_back({plane_cost(h, p % h->Q), p});
+  lpt_schedule(h->info.wg, cost, &h->sched);
+}
+
 namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -261,8 +283,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// One 4D tiled descriptor (x, y, z, plane) per buffer and staged box shape.
-int build_maps(olb_ctx* h) {
+// 4D tiled descriptors (x, y, z, plane) of one padded buffer of `nplanes`
+// planes, one per staged box shape.
+int encode_maps(olb_ctx* h, void* buffer, int nplanes, CUtensorMap out[4]) {
   auto enc = encode_fn();
   if (!enc) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled is not available");
   CUtensorMapDataType dt;
@@ -273,19 +296,25 @@ int build_maps(olb_ctx* h) {
     default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
   }
   const Padded& P = h->pad;
-  const cuuint64_t dims[4] = {(cuuint64_t)P.np[0], (cuuint64_t)P.np[1], (cuuint64_t)P.np[2], (cuuint64_t)h->planes};
+  const cuuint64_t dims[4] = {(cuuint64_t)P.np[0], (cuuint64_t)P.np[1], (cuuint64_t)P.np[2], (cuuint64_t)nplanes};
   const cuuint64_t strides[3] = {(cuuint64_t)P.np[0] * h->elem, (cuuint64_t)P.np[0] * P.np[1] * h->elem,
                                  (cuuint64_t)P.plane * h->elem};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  for (int b = 0; b < 2; ++b)
-    for (int v = 0; v < 4; ++v) {
-      const cuuint32_t box[4] = {(cuuint32_t)h->info.bxw, (cuuint32_t)((v & 1) ? h->info.by : h->info.ty),
-                                 (cuuint32_t)((v & 2) ? h->info.bz : h->info.tz), 1};
-      CUresult r = enc(&h->maps.m[b][v], dt, 4, h->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
-    }
+  for (int v = 0; v < 4; ++v) {
+    const cuuint32_t box[4] = {(cuuint32_t)h->info.bxw, (cuuint32_t)((v & 1) ? h->info.by : h->info.ty),
+                               (cuuint32_t)((v & 2) ? h->info.bz : h->info.tz), 1};
+    CUresult r = enc(&out[v], dt, 4, buffer, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  }
+  return OLB_OK;
+}
+
+int build_maps(olb_ctx* h) {
+  for (int b = 0; b < 2; ++b) {
+    const int rc = encode_maps(h, h->buf[b], h->planes, h->maps.m[b]);
+    if (rc) return rc;
+  }
   return OLB_OK;
 }
 
@@ -353,6 +382,167 @@ int launch_rc(int rc, const char* what) {
   if (rc == 0) return OLB_OK;
   if (rc < 0) return fail(OLB_EUNSUPPORTED, std::string(what) + ": configuration not built");
   return cuda_fail((cudaError_t)rc, what);
+}
+
+// Launch description of the forward step on the handle's buffers.
+StepLaunch base_launch(olb_ctx* h) {
+  StepLaunch L{};
+  L.a = h->args;
+  L.D = h->D;
+  L.P = h->p;
+  L.storage = h->storage;
+  L.compressible = h->comp;
+  L.veltab = h->veltab.data();
+  L.stentab = h->stentab.data();
+  L.stentab2 = nullptr;
+  L.maps = &h->maps;
+  L.sched = &h->sched;
+  L.grid = h->step_grid;
+  L.force_generic = h->force_generic;
+  L.stream = h->stream;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the isothermal step
+// ---------------------------------------------------------------------------
+
+size_t adj_elem(const olb_ctx* h) { return h->storage == OLB_FP64 ? sizeof(double) : sizeof(float); }
+
+// Stencils of the adjoint input: the reflected stencil (transpose of the
+// pull: first point -(m0 + p), weights in reverse order, same axes) and the
+// identity (no axis active).
+template <typename C, int P1>
+void fill_adj_tabs_p(olb_ctx* h) {
+  h->st_refl = h->stentab;
+  h->st_id.assign(sizeof(StencilTab<C, P1>), 0);
+  auto* r = reinterpret_cast<StencilTab<C, P1>*>(h->st_refl.data());
+  auto* id = reinterpret_cast<StencilTab<C, P1>*>(h->st_id.data());
+  const int p = h->p;
+  for (int i = 0; i < h->Q; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      r->m0[i][a] = -h->m0[i * 3 + a] - p;
+      for (int j = 0; j <= p; ++j) r->W[i][a][j] = (C)h->W[(i * 3 + a) * (p + 1) + (p - j)];
+      id->m0[i][a] = 0;
+      id->W[i][a][0] = (C)1;
+    }
+    id->active[i] = 0;
+  }
+}
+
+template <typename C>
+void fill_adj_tabs(olb_ctx* h) {
+  if (h->p == 3) fill_adj_tabs_p<C, 4>(h);
+  else fill_adj_tabs_p<C, 5>(h);
+}
+
+// Buffers, tables and schedules of the adjoint sweep (once per handle).
+int adj_prepare(olb_ctx* h) {
+  if (h->adj_ready) return OLB_OK;
+  if (h->comp) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the isothermal step only");
+  if (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED)
+    return fail(OLB_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage");
+  if (h->info.wg == 0 || (h->p != 3 && h->p != 4))
+    return fail(OLB_EUNSUPPORTED, "the adjoint needs the two-phase kernel (p = 3 or 4, automatic kernel choice)");
+  // the reflected stencil must stay inside the ghost layers
+  for (int i = 0; i < h->Q; ++i)
+    for (int a = 0; a < h->D; ++a) {
+      if (h->set.xi[i][a] == 0.0) continue;
+      const int m0 = h->m0[i * 3 + a];
+      if (m0 + h->p > h->pad.gl[a] || -m0 > h->pad.gr[a])
+        return fail(OLB_EUNSUPPORTED, "reflected stencil reaches beyond the ghost layers (asymmetric set)");
+    }
+  if (h->storage == OLB_FP64) fill_adj_tabs<double>(h);
+  else fill_adj_tabs<float>(h);
+  const size_t bytes = (size_t)h->Q * h->pad.plane * h->elem;
+  for (int k = 0; k < 2; ++k) {
+    if (h->adj[k]) continue;
+    cudaError_t e = cudaMalloc(&h->adj[k], bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->adj[k], 0, bytes, h->stream);
+    if (e != cudaSuccess) return fail(OLB_ENOMEM, "adjoint buffers: " + std::string(cudaGetErrorString(e)));
+    const int rc = encode_maps(h, h->adj[k], h->Q, h->adj_maps.m[k]);
+    if (rc) return rc;
+  }
+  if (!h->adj_scratch) {
+    const size_t sb = (size_t)h->step_grid * 2 * h->Q * h->info.tile * adj_elem(h);
+    cudaError_t e = cudaMalloc(&h->adj_scratch, sb);
+    if (e != cudaSuccess) return fail(OLB_ENOMEM, "adjoint staging: " + std::string(cudaGetErrorString(e)));
+  }
+  std::vector<std::pair<double, int>> first, mid, last;
+  for (int i = 0; i < h->Q; ++i) {
+    const double c = plane_cost(h, i);
+    first.push_back({c, i});
+    first.push_back({1.0, h->Q + i});
+    mid.push_back({c, i});
+    mid.push_back({c, h->Q + i});
+    last.push_back({c, h->Q + i});
+  }
+  lpt_schedule(h->info.wg, first, &h->sched_adj[0]);
+  lpt_schedule(h->info.wg, mid, &h->sched_adj[1]);
+  lpt_schedule(h->info.wg, last, &h->sched_adj[2]);
+  h->adj_ready = 1;
+  return OLB_OK;
+}
+
+// One launch of the adjoint kernel: adjoint input adj[in], output adj[out],
+// forward state `fwd` (a tape slot; null in mode 2).
+int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, const WgSchedule* sch, int slot, int in,
+               int out) {
+  StepLaunch L = base_launch(h);
+  L.a.buf[0] = slot >= 0 ? h->tape[slot] : h->adj[in];
+  L.a.buf[1] = h->adj[out];
+  L.a.src = 0;
+  L.a.scratch = h->adj_scratch;
+  L.a.planes = 2 * h->Q;
+  L.a.reduce = 0;
+  L.a.mode = mode;
+  TmaMaps M;
+  std::memcpy(M.m[0], slot >= 0 ? h->tape_maps[slot].m[0] : h->adj_maps.m[in], sizeof(M.m[0]));
+  std::memcpy(M.m[1], h->adj_maps.m[in], sizeof(M.m[1]));
+  L.stentab2 = st2.data();
+  L.maps = &M;
+  L.sched = sch;
+  int r;
+  if (h->storage == OLB_FP64) r = h->D == 2 ? launch_adj_f64_2d(L) : launch_adj_f64_3d(L);
+  else r = h->D == 2 ? launch_adj_f32_2d(L) : launch_adj_f32_3d(L);
+  return launch_rc(r, "sl_adjoint");
+}
+
+// Adjoint sweep over the forward states in `slots` (the input of the last
+// step first).  lam_dev (compact [Q][n], adjoint type): on entry dJ/d(state
+// after the last step), on return dJ/d(state before the first step).
+int adjoint_sweep(olb_ctx* h, const std::vector<int>& slots, void* lam_dev) {
+  int rc = launch_rc(launch_scatter(h->aux, h->adj[0], lam_dev, h->stream), "adjoint scatter");
+  if (rc) return rc;
+  int cur = 0;
+  for (size_t k = 0; k < slots.size(); ++k) {
+    const bool first = k == 0;
+    rc = adj_launch(h, 1, first ? h->st_id : h->st_refl, &h->sched_adj[first ? 0 : 1], slots[k], cur, cur ^ 1);
+    if (rc) return rc;
+    cur ^= 1;
+  }
+  rc = adj_launch(h, 2, h->st_refl, &h->sched_adj[2], -1, cur, cur ^ 1);
+  if (rc) return rc;
+  cur ^= 1;
+  return launch_rc(launch_gather(h->aux, h->adj[cur], lam_dev, h->stream), "adjoint gather");
+}
+
+int tape_grow(olb_ctx* h, int nslots) {
+  const size_t bytes = (size_t)h->planes * h->pad.plane * h->elem;
+  while ((int)h->tape.size() < nslots) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, h->stream);
+    if (e != cudaSuccess) {
+      if (p) cudaFree(p);
+      return fail(OLB_ENOMEM, "tape slot: " + std::string(cudaGetErrorString(e)));
+    }
+    h->tape.push_back(p);
+    h->tape_maps.emplace_back();
+    const int rc = encode_maps(h, p, h->planes, h->tape_maps.back().m[0]);
+    if (rc) return rc;
+  }
+  return OLB_OK;
 }
 
 }  // namespace
@@ -666,19 +856,7 @@ int olb_step(olb_handle h, int n) {
   if (n < 0) return fail(OLB_EINVAL, "negative step count");
   int rc = set_device(h);
   if (rc) return rc;
-  StepLaunch L;
-  L.a = h->args;
-  L.D = h->D;
-  L.P = h->p;
-  L.storage = h->storage;
-  L.compressible = h->comp;
-  L.veltab = h->veltab.data();
-  L.stentab = h->stentab.data();
-  L.maps = &h->maps;
-  L.sched = &h->sched;
-  L.grid = h->step_grid;
-  L.force_generic = h->force_generic;
-  L.stream = h->stream;
+  StepLaunch L = base_launch(h);
   for (int s = 0; s < n; ++s) {
     const long long count = h->step_count + 1;
     L.a.src = h->cur;
@@ -872,6 +1050,159 @@ int olb_synchronize(olb_handle h, int timeout_ms) {
   rc = stream_sync(h, timeout_ms);
   if (rc) return rc;
   return check_err(h);
+}
+
+int olb_tape_reserve(olb_handle h, int nslots) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (nslots < 1) return fail(OLB_EINVAL, "the tape needs at least one slot");
+  int rc = set_device(h);
+  if (rc) return rc;
+  rc = adj_prepare(h);
+  if (rc) return rc;
+  return tape_grow(h, nslots);
+}
+
+int olb_tape_record(olb_handle h, int n) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (n < 0) return fail(OLB_EINVAL, "negative step count");
+  if (n + 1 > (int)h->tape.size()) return fail(OLB_EBOUNDS, "tape has fewer than n + 1 slots");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->planes * h->pad.plane * h->elem;
+  cudaError_t e = cudaMemcpyAsync(h->tape[0], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tape copy");
+  StepLaunch L = base_launch(h);
+  L.a.reduce = 0;
+  L.a.src = 0;
+  for (int s = 1; s <= n; ++s) {
+    L.a.buf[0] = h->tape[s - 1];
+    L.a.buf[1] = h->tape[s];
+    L.maps = &h->tape_maps[s - 1];
+    rc = launch_rc(launch_step(h->storage, h->D, L), "sl_step (tape)");
+    if (rc) return rc;
+  }
+  e = cudaMemcpyAsync(h->buf[h->cur], h->tape[n], bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tape copy");
+  h->step_count += n;
+  h->partials_valid = 0;
+  h->tape_len = n + 1;
+  return OLB_OK;
+}
+
+int olb_tape_adjoint(olb_handle h, void* lambda, int n, int on_device) {
+  if (!h || !lambda) return fail(OLB_EINVAL, "null handle or adjoint buffer");
+  const int L = h->tape_len - 1;
+  if (n < 1 || n > L) return fail(OLB_EBOUNDS, "n must be between 1 and the number of recorded steps");
+  int rc = set_device(h);
+  if (rc) return rc;
+  rc = adj_prepare(h);
+  if (rc) return rc;
+  std::vector<int> slots;
+  for (int k = L; k > L - n; --k) slots.push_back(k - 1);
+  const size_t bytes = (size_t)h->Q * h->nnodes * adj_elem(h);
+  void* lam = lambda;
+  if (!on_device) {
+    rc = dev_alloc(h, &lam, bytes);
+    if (rc) return rc;
+    cudaMemcpyAsync(lam, lambda, bytes, cudaMemcpyHostToDevice, h->stream);
+  }
+  rc = adjoint_sweep(h, slots, lam);
+  if (!on_device) {
+    if (rc == OLB_OK) rc = copy_out(h, lambda, lam, bytes, 0);
+    cudaFreeAsync(lam, h->stream);
+    if (rc == OLB_OK) rc = check_err(h);
+  }
+  return rc;
+}
+
+int olb_adjoint_step(olb_handle h, const void* fwd_state, void* lambda, int on_device) {
+  if (!h || !fwd_state || !lambda) return fail(OLB_EINVAL, "null handle, state or adjoint buffer");
+  int rc = set_device(h);
+  if (rc) return rc;
+  rc = adj_prepare(h);
+  if (rc) return rc;
+  rc = tape_grow(h, 1);
+  if (rc) return rc;
+  const size_t sbytes = (size_t)h->planes * h->nnodes * h->elem;
+  const size_t lbytes = (size_t)h->Q * h->nnodes * adj_elem(h);
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, sbytes + lbytes);
+    if (rc) return rc;
+    cudaMemcpyAsync(tmp, fwd_state, sbytes, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(static_cast<char*>(tmp) + sbytes, lambda, lbytes, cudaMemcpyHostToDevice, h->stream);
+  }
+  const void* fs = on_device ? fwd_state : tmp;
+  void* lam = on_device ? lambda : static_cast<char*>(tmp) + sbytes;
+  rc = launch_rc(launch_scatter(h->aux, h->tape[0], fs, h->stream), "adjoint state scatter");
+  h->tape_len = 0;  // slot 0 no longer holds a recorded trajectory
+  if (rc == OLB_OK) rc = adjoint_sweep(h, std::vector<int>{0}, lam);
+  if (!on_device) {
+    if (rc == OLB_OK) rc = copy_out(h, lambda, lam, lbytes, 0);
+    cudaFreeAsync(tmp, h->stream);
+    if (rc == OLB_OK) rc = check_err(h);
+  }
+  return rc;
+}
+
+int olb_moments_vjp(olb_handle h, const double* grad_rho, const double* grad_u, void* lambda, int on_device) {
+  if (!h || !lambda) return fail(OLB_EINVAL, "null handle or adjoint buffer");
+  if (h->comp || (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED))
+    return fail(OLB_EUNSUPPORTED, "the adjoint is built for the isothermal step in FP64 and FP32 storage");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->nnodes;
+  const size_t lbytes = (size_t)h->Q * n * adj_elem(h);
+  const double *gr = grad_rho, *gu = grad_u;
+  void* lam = lambda;
+  void* tmp = nullptr;
+  if (!on_device) {
+    rc = dev_alloc(h, &tmp, lbytes + n * (1 + h->D) * sizeof(double));
+    if (rc) return rc;
+    double* t = reinterpret_cast<double*>(static_cast<char*>(tmp) + lbytes);
+    lam = tmp;
+    if (grad_rho) cudaMemcpyAsync(t, grad_rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (grad_u) cudaMemcpyAsync(t + n, grad_u, n * h->D * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    gr = grad_rho ? t : nullptr;
+    gu = grad_u ? t + n : nullptr;
+  }
+  rc = launch_rc(launch_moments_vjp(h->aux, h->buf[h->cur], gr, gu, lam, h->stream), "moments_vjp");
+  if (!on_device) {
+    if (rc == OLB_OK) rc = copy_out(h, lambda, lam, lbytes, 0);
+    cudaFreeAsync(tmp, h->stream);
+  }
+  return rc;
+}
+
+int olb_equilibrium_vjp(olb_handle h, const double* rho, const double* u, const void* lambda, double* grad_rho,
+                        double* grad_u, int on_device) {
+  if (!h || !rho || !u || !lambda || !grad_rho || !grad_u) return fail(OLB_EINVAL, "null argument");
+  if (h->comp || (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED))
+    return fail(OLB_EUNSUPPORTED, "the adjoint is built for the isothermal step in FP64 and FP32 storage");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->nnodes;
+  const size_t lbytes = (size_t)h->Q * n * adj_elem(h);
+  const size_t fbytes = n * (1 + h->D) * sizeof(double);
+  if (on_device)
+    return launch_rc(launch_equilibrium_vjp(h->aux, rho, u, lambda, grad_rho, grad_u, h->stream), "equilibrium_vjp");
+  void* tmp = nullptr;
+  rc = dev_alloc(h, &tmp, lbytes + 2 * fbytes);
+  if (rc) return rc;
+  char* c = static_cast<char*>(tmp);
+  double* din = reinterpret_cast<double*>(c + lbytes);
+  double* dout = reinterpret_cast<double*>(c + lbytes + fbytes);
+  cudaMemcpyAsync(c, lambda, lbytes, cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(din, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(din + n, u, n * h->D * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  rc = launch_rc(launch_equilibrium_vjp(h->aux, din, din + n, c, dout, dout + n, h->stream), "equilibrium_vjp");
+  if (rc == OLB_OK) {
+    cudaMemcpyAsync(grad_rho, dout, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    rc = copy_out(h, grad_u, dout + n, n * h->D * sizeof(double), 0);
+  }
+  cudaFreeAsync(tmp, h->stream);
+  if (rc == OLB_OK) rc = stream_sync(h, 0);
+  return rc;
 }
 
 const char* olb_strerror(int code) {

@@ -94,6 +94,7 @@ struct StepArgs {
   int ntiles;
   int Q, planes, N;
   int reduce;           // 1: accumulate the global sums this step
+  int mode;             // adjoint kernel: 1 transposed collision, 2 transposed pull only
   int quad_ok;          // n[0] % 4 == 0: 4-node x groups never straddle the edge
   double rho_ref;       // rho0 for shifted storage, 0 for FP64
   double inv_tau;       // isothermal 1/tau
@@ -116,6 +117,7 @@ struct StepLaunch {
   int D, P, storage, compressible;
   const void* veltab;   // VelTab<C>
   const void* stentab;  // StencilTab<C, P+1>
+  const void* stentab2; // adjoint kernel: stencil of the adjoint input (reflected or identity)
   const TmaMaps* maps;
   const WgSchedule* sched;
   int grid;             // CTAs
@@ -141,6 +143,13 @@ struct StepInfo {
   int bxw, by, bz, tile, tx, ty, tz, vec;
   int wg;  // warpgroups of the two-phase kernel (0: the single-role kernel runs)
 };
+// Adjoint step of the isothermal two-phase kernel (FP64 and FP32 storage);
+// -1 when the configuration is not built.
+int launch_adj_f64_2d(const StepLaunch& L);
+int launch_adj_f64_3d(const StepLaunch& L);
+int launch_adj_f32_2d(const StepLaunch& L);
+int launch_adj_f32_3d(const StepLaunch& L);
+
 int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f64_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f32_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
@@ -172,5 +181,11 @@ int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream
 int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream);
 int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream);
 int launch_reduce_final(const double* partials, int nslots, double* out, void* stream);
+// Adjoint seed and initial-state gradients (FP64 and FP32 storage; -1 otherwise).
+// lam is compact [Q][z][y][x] in the adjoint type (double / float).
+int launch_moments_vjp(const AuxArgs& a, const void* state, const double* grad_rho, const double* grad_u, void* lam,
+                       void* stream);
+int launch_equilibrium_vjp(const AuxArgs& a, const double* rho, const double* u, const void* lam, double* grad_rho,
+                           double* grad_u, void* stream);
 
 }  // namespace olb

@@ -138,4 +138,14 @@ int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   return -1;
 }
 
+int launch_adj_f64_2d(const StepLaunch& L) {
+  if (L.P == 3 && L.a.N == 2 && L.a.Q <= 9) return wg::launch_adj<2, 3, S, 9, 2>(L);
+  if (L.P == 3 && L.a.N == 2) return wg::launch_adj<2, 3, S, 27, 2>(L);
+  if (L.P == 3 && L.a.N == 3) return wg::launch_adj<2, 3, S, 27, 3>(L);
+  if (L.P == 4 && L.a.N == 2 && L.a.Q <= 9) return wg::launch_adj<2, 4, S, 9, 2>(L);
+  if (L.P == 4 && L.a.N == 2) return wg::launch_adj<2, 4, S, 27, 2>(L);
+  if (L.P == 4 && L.a.N == 3) return wg::launch_adj<2, 4, S, 27, 3>(L);
+  return -1;
+}
+
 }  // namespace olb

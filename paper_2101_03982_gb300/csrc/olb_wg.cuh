@@ -155,11 +155,80 @@ __device__ __forceinline__ C phi_n(C s, C q, C t, C rD, C rpoly) {
   return v;
 }
 
-template <int D, int P, typename S, bool COMP, int QM, int N>
-__global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
-    sl_wg_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
-                 const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
-                 const __grid_constant__ TmaMaps maps, const __grid_constant__ WgSchedule sched) {
+// d Phi/ds and d Phi/dq of the isothermal closed form of order N (theta = 1):
+// Phi = s + (s^2 - q)/2 [+ s (s^2 - 3q)/6] [+ (s^4 - 6 s^2 q + 3 q^2)/24].
+template <typename C, int N>
+__device__ __forceinline__ void phi_grad(C s, C q, C& ph, C& ps, C& pq) {
+  const C s2 = s * s;
+  ph = fma(C(0.5), s2 - q, s);
+  ps = C(1) + s;
+  pq = C(-0.5);
+  if (N >= 3) {
+    ph = fma(C(1.0 / 6.0), s * (s2 - C(3) * q), ph);
+    ps = fma(C(0.5), s2 - q, ps);
+    pq = fma(C(-0.5), s, pq);
+  }
+  if (N >= 4) {
+    ph = fma(C(1.0 / 24.0), s2 * s2 - C(6) * s2 * q + C(3) * q * q, ph);
+    ps = fma(C(1.0 / 6.0), s * (s2 - C(3) * q), ps);
+    pq = fma(C(0.25), q - s2, pq);
+  }
+}
+
+// Periodic copies of one node in the ghost layers: 0, 1 (one axis), 3 (two
+// axes) or 7 (three axes) plane offsets, the single-axis ones first.
+struct Images {
+  int n;
+  int i0, i1, i2, i3, i4, i5, i6;
+  bool many;  // an axis shorter than its two ghost widths: every copy is stored
+  static __device__ __forceinline__ Images make(int sx, int sy, int sz, bool simple) {
+    Images m;
+    const int nax = (sx != 0) + (sy != 0) + (sz != 0);
+    m.n = nax == 0 ? 0 : (nax == 1 ? 1 : (nax == 2 ? 3 : 7));
+    const int a0 = sx ? sx : (sy ? sy : sz);
+    const int a1 = sx ? (sy ? sy : sz) : (sy ? sz : 0);
+    m.i0 = a0;
+    m.i1 = a1;
+    m.i2 = nax == 3 ? sz : a0 + a1;
+    m.i3 = sx + sy;
+    m.i4 = sx + sz;
+    m.i5 = sy + sz;
+    m.i6 = sx + sy + sz;
+    m.many = !simple && m.n > 0;
+    return m;
+  }
+  // store v at p (the node's address in its plane) and at its copies
+  template <typename S>
+  __device__ __forceinline__ void put(S* p, S v, const Padded& pd, long long off, int x, int y, int z) const {
+    p[0] = v;
+    if (!n) return;
+    if (many) {
+      store_all_images(p - off, pd, x, y, z, v);
+      return;
+    }
+    p[i0] = v;
+    if (n > 1) {
+      p[i1] = v;
+      p[i2] = v;
+      if (n > 3) {
+        p[i3] = v;
+        p[i4] = v;
+        p[i5] = v;
+        p[i6] = v;
+      }
+    }
+  }
+};
+
+// Body of the two-phase kernels.  ADJ = false: the forward step.  ADJ = true:
+// one adjoint step (see sl_adj_kernel); planes q < Q are pulled from the
+// forward state with the stencil st, planes Q + i from the adjoint input with
+// the stencil st2, through the tensor maps maps.m[0] and maps.m[1].
+template <int D, int P, typename S, bool COMP, int QM, int N, bool ADJ>
+__device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename Store<S>::C>& vt,
+                                        const StencilTab<typename Store<S>::C, P + 1>& st,
+                                        const StencilTab<typename Store<S>::C, P + 1>& st2, const TmaMaps& maps,
+                                        const WgSchedule& sched) {
   using L = GLayout<D, P, S>;
   using C = typename Store<S>::C;
   using PR = Pr<C>;
@@ -185,14 +254,19 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
   C* __restrict__ scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE;
   const unsigned long long keep = policy_evict_last();
 
+  // stencil table, tensor maps and tensor plane of a staged plane
+  auto tab_of = [&](int plane) -> const StencilTab<C, P + 1>& { return (ADJ && plane >= Q) ? st2 : st; };
+  auto maps_of = [&](int plane) -> const CUtensorMap* { return (ADJ && plane >= Q) ? maps.m[1] : maps4; };
+  auto tplane_of = [&](int plane) { return (ADJ && plane >= Q) ? plane - Q : plane; };
   auto box_coords = [&](int tile, int plane, int& X, int& Y, int& Z) {
     const int tx = tile % a.nt[0], r = tile / a.nt[0];
     const int i = plane < Q ? plane : plane - Q;
-    const int act = st.active[i];
-    X = tx * L::TX + pd.gl[0] + ((act & 1) ? st.m0[i][0] : 0);
+    const auto& T = tab_of(plane);
+    const int act = T.active[i];
+    X = tx * L::TX + pd.gl[0] + ((act & 1) ? T.m0[i][0] : 0);
     X -= X % L::VEC;
-    Y = (r % a.nt[1]) * L::TY + pd.gl[1] + ((act & 2) ? st.m0[i][1] : 0);
-    Z = D == 3 ? (r / a.nt[1]) * L::TZ + pd.gl[2] + ((act & 4) ? st.m0[i][2] : 0) : 0;
+    Y = (r % a.nt[1]) * L::TY + pd.gl[1] + ((act & 2) ? T.m0[i][1] : 0);
+    Z = D == 3 ? (r / a.nt[1]) * L::TZ + pd.gl[2] + ((act & 4) ? T.m0[i][2] : 0) : 0;
     return ((act & 2) ? 1 : 0) | ((D == 3 && (act & 4)) ? 2 : 0);
   };
   auto issue = [&](int tile, int plane) {
@@ -201,12 +275,12 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
     const unsigned bytes = (unsigned)(L::BXW * ((v & 1) ? L::BY : L::TY) * ((v & 2) ? L::BZ : L::TZ) * sizeof(S));
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(bar, bytes);
-    tma_load_4d(box, &maps4[v], X, Y, Z, plane, bar);
+    tma_load_4d(box, &maps_of(plane)[v], X, Y, Z, tplane_of(plane), bar);
   };
   auto prefetch = [&](int tile, int plane) {
     int X, Y, Z;
     const int v = box_coords(tile, plane, X, Y, Z);
-    tma_prefetch_4d(&maps4[v], X, Y, Z, plane);
+    tma_prefetch_4d(&maps_of(plane)[v], X, Y, Z, tplane_of(plane));
   };
 
   if (wt == 0) mbar_init(bar, 1);
@@ -241,7 +315,8 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       parity ^= 1u;
       pending = false;
       const int i = plane < Q ? plane : plane - Q;
-      const int act = st.active[i];
+      const auto& T = tab_of(plane);
+      const int act = T.active[i];
       const bool zact = D == 3 && (act & 4), yact = (act & 2) != 0, xact = (act & 1) != 0;
       if (wt == 0) {
         // warm L2 with the plane after next
@@ -253,7 +328,7 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       if (zact) {
         T2 W[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) W[j] = PR::set(st.W[i][2][j]);
+        for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][2][j]);
         const int BYA = yact ? L::BY : L::TY;
         const int items = L::NQX * BYA * (L::TZ / L::ZCH);
         const int PLs = BYA * L::BXW;
@@ -282,7 +357,7 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       if (yact) {
         T2 W[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) W[j] = PR::set(st.W[i][1][j]);
+        for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][1][j]);
         constexpr int NYC = L::TY / L::YCH;
         constexpr int items = L::NQX * L::TZ * NYC;
         for (int item = wt; item < items; item += WGT) {
@@ -316,8 +391,8 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       {
         C W[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) W[j] = st.W[i][0][j];
-        const int xo = xact ? ((st.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
+        for (int j = 0; j <= P; ++j) W[j] = T.W[i][0][j];
+        const int xo = xact ? ((T.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
         constexpr int QPT = L::TILE / 4 / WGT;  // 4-node x groups per thread
 #pragma unroll
         for (int m = 0; m < QPT; ++m) {
@@ -348,10 +423,18 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
     // ---------------- phase B: collide every node of the tile ---------------
     const int tx = tile % a.nt[0], tr = tile / a.nt[0];
     const int ty = tr % a.nt[1], tz = tr / a.nt[1];
-    const bool red = a.reduce != 0;
+    const bool red = !ADJ && a.reduce != 0;
     C tsum[NRED];
 #pragma unroll
     for (int c = 0; c < NRED; ++c) tsum[c] = C(0);
+
+    // periodic copies of node (x, y, z) in the ghost layers (0, 1, 3 or 7)
+    auto images_of = [&](int x, int y, int z) {
+      const int dx = one_image(x, pd.n[0], pd.gl[0], pd.gr[0]);
+      const int dy = one_image(y, pd.n[1], pd.gl[1], pd.gr[1]);
+      const int dz = D == 3 ? one_image(z, pd.n[2], pd.gl[2], pd.gr[2]) : 0;
+      return Images::make(dx, dy * pd.np[0], dz * pd.np[0] * pd.np[1], simple);
+    };
 
     auto collide = [&](int n, auto RED) {
       constexpr bool R = decltype(RED)::value;
@@ -409,21 +492,10 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
         gA = fma(rho, tt, A);
         rth = rho * theta;
       }
-      // periodic copies of this node in the ghost layers: 0, 1, 3 or 7 of them
-      const int dx = one_image(x, pd.n[0], pd.gl[0], pd.gr[0]);
-      const int dy = one_image(y, pd.n[1], pd.gl[1], pd.gr[1]);
-      const int dz = D == 3 ? one_image(z, pd.n[2], pd.gl[2], pd.gr[2]) : 0;
-      const int sx = dx, sy = dy * pd.np[0], sz = dz * pd.np[0] * pd.np[1];
-      // image offsets: the single-axis ones, then the pairs, then the corner
-      const int nax = (sx != 0) + (sy != 0) + (sz != 0);
-      const int nimg = nax == 0 ? 0 : (nax == 1 ? 1 : (nax == 2 ? 3 : 7));
-      const int a0 = sx ? sx : (sy ? sy : sz);
-      const int a1 = sx ? (sy ? sy : sz) : (sy ? sz : 0);
-      const int i0 = a0, i1 = a1, i2 = nax == 3 ? sz : a0 + a1;
-      const int i3 = sx + sy, i4 = sx + sz, i5 = sy + sz, i6 = sx + sy + sz;
-      const bool many = !simple && nimg > 0;  // tiny grid: several copies per axis
+      const Images im = images_of(x, y, z);
+      const long long off = pad_index(pd, x, y, z);
       // equilibrium (Appendix A), BGK (Sec. 3) and the stores
-      S* pf = dst + pad_index(pd, x, y, z);
+      S* pf = dst + off;
       C Pi[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
@@ -434,48 +506,11 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
         const C ph = phi_n<C, COMP, N>(s, q, tt, vt.rD[i], vt.rpoly[i]);
         const C feqd = vt.w[i] * fma(rho, ph, A);
         const C fneq = f[i] - feqd;
-        const S o = Store<S>::st(fma(-fneq, itau, f[i]));
-        pf[0] = o;
+        im.put(pf, Store<S>::st(fma(-fneq, itau, f[i])), pd, off, x, y, z);
         if (COMP) {
           const C gv = scr[(size_t)(Q + i) * L::TILE + n];
           const C geqd = vt.w[i] * sc.gfac * fma(rth, ph, gA);
-          const S og = Store<S>::st(fma(-(gv - geqd), itau, gv));
-          S* pg = pf + (long long)Q * pd.plane;
-          pg[0] = og;
-          if (nimg) {
-            if (many) {
-              store_all_images(pg - pad_index(pd, x, y, z), pd, x, y, z, og);
-            } else {
-              pg[i0] = og;
-              if (nimg > 1) {
-                pg[i1] = og;
-                pg[i2] = og;
-                if (nimg > 3) {
-                  pg[i3] = og;
-                  pg[i4] = og;
-                  pg[i5] = og;
-                  pg[i6] = og;
-                }
-              }
-            }
-          }
-        }
-        if (nimg) {
-          if (many) {
-            store_all_images(pf - pad_index(pd, x, y, z), pd, x, y, z, o);
-          } else {
-            pf[i0] = o;
-            if (nimg > 1) {
-              pf[i1] = o;
-              pf[i2] = o;
-              if (nimg > 3) {
-                pf[i3] = o;
-                pf[i4] = o;
-                pf[i5] = o;
-                pf[i6] = o;
-              }
-            }
-          }
+          im.put(pf + (long long)Q * pd.plane, Store<S>::st(fma(-(gv - geqd), itau, gv)), pd, off, x, y, z);
         }
         pf += pd.plane;
         if (R) {
@@ -503,10 +538,84 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       }
     };
 
-    if (red) {
-      for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, true>());
+    // adjoint of the collision of one node (isothermal): staged planes
+    // q < Q hold the pulled forward populations f~, planes Q + i the pulled
+    // adjoint sigma_i.  mu_k = (1 - 1/tau) sigma_k + (a + b . xi^_k) / tau with
+    // a = sum_i w_i sigma_i (1 + Phi_i - s_i dPhi/ds - 2 q dPhi/dq) and
+    // b = sum_i w_i sigma_i (dPhi/ds xi^_i + 2 dPhi/dq u^).  Mode 2 copies sigma.
+    auto adjoint = [&](int n) {
+      const int lx = n % L::TX, ly = (n / L::TX) % L::TY, lz = n / (L::TX * L::TY);
+      const int x = tx * L::TX + lx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
+      if (x >= pd.n[0] || y >= pd.n[1] || z >= pd.n[2]) return;
+      const Images im = images_of(x, y, z);
+      const long long off = pad_index(pd, x, y, z);
+      S* pf = dst + off;
+      const C* sg = scr + (size_t)Q * L::TILE + n;
+      if (a.mode == 2) {
+#pragma unroll
+        for (int i = 0; i < QM; ++i) {
+          if (i >= Q) break;
+          im.put(pf, Store<S>::st(sg[(size_t)i * L::TILE]), pd, off, x, y, z);
+          pf += pd.plane;
+        }
+        return;
+      }
+      C A = C(0), jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        const C ft = scr[(size_t)i * L::TILE + n];
+        A += ft;
+        jx = fma(vt.xi[i][0], ft, jx);
+        jy = fma(vt.xi[i][1], ft, jy);
+        if (D == 3) jz = fma(vt.xi[i][2], ft, jz);
+      }
+      C sig[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) sig[i] = i < Q ? sg[(size_t)i * L::TILE] : C(0);
+      const C ir = C(1) / (sc.rho_ref + A);
+      const C uhx = jx * ir * sc.inv_cs, uhy = jy * ir * sc.inv_cs, uhz = jz * ir * sc.inv_cs;
+      const C q = uhx * uhx + uhy * uhy + uhz * uhz;
+      C ca = C(0), bx = C(0), by = C(0), bz = C(0), bq = C(0);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        C s = vt.xih[i][0] * uhx;
+        s = fma(vt.xih[i][1], uhy, s);
+        if (D == 3) s = fma(vt.xih[i][2], uhz, s);
+        C ph, ps, pq;
+        phi_grad<C, N>(s, q, ph, ps, pq);
+        const C v = vt.w[i] * sig[i];
+        ca = fma(v, C(1) + ph - s * ps - C(2) * q * pq, ca);
+        const C vs = v * ps;
+        bx = fma(vs, vt.xih[i][0], bx);
+        by = fma(vs, vt.xih[i][1], by);
+        if (D == 3) bz = fma(vs, vt.xih[i][2], bz);
+        bq = fma(C(2) * v, pq, bq);
+      }
+      bx = fma(bq, uhx, bx);
+      by = fma(bq, uhy, by);
+      bz = fma(bq, uhz, bz);
+      const C keep_s = C(1) - sc.inv_tau;
+#pragma unroll
+      for (int k = 0; k < QM; ++k) {
+        if (k >= Q) break;
+        C g = fma(bx, vt.xih[k][0], ca);
+        g = fma(by, vt.xih[k][1], g);
+        if (D == 3) g = fma(bz, vt.xih[k][2], g);
+        im.put(pf, Store<S>::st(fma(keep_s, sig[k], g * sc.inv_tau)), pd, off, x, y, z);
+        pf += pd.plane;
+      }
+    };
+
+    if constexpr (ADJ) {
+      for (int n = tid; n < L::TILE; n += NT) adjoint(n);
     } else {
-      for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, false>());
+      if (red) {
+        for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, true>());
+      } else {
+        for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, false>());
+      }
     }
     if (red) {
 #pragma unroll
@@ -525,7 +634,7 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
     if (wt == 0 && pending) mbar_wait_bounded(bar, parity);  // let the copy in flight land
     return;
   }
-  if (a.reduce) {
+  if (!ADJ && a.reduce) {
     __syncthreads();
     if (tid < NRED) {
       double s = 0.0;
@@ -533,6 +642,50 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
       a.partials[(size_t)blockIdx.x * NRED + tid] = s;
     }
   }
+}
+
+// Forward step (Sec. 3): pull, moments, equilibrium, BGK, global sums.
+template <int D, int P, typename S, bool COMP, int QM, int N>
+__global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
+    sl_wg_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
+                 const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
+                 const __grid_constant__ TmaMaps maps, const __grid_constant__ WgSchedule sched) {
+  wg_body<D, P, S, COMP, QM, N, false>(a, vt, st, st, maps, sched);
+}
+
+// One step of the adjoint sweep of the isothermal step, in terms of
+// mu_t = dJ/d(pulled populations of step t):
+//   mu_{t-1} = Jc(f~_{t-1})^T S^T mu_t,  f~_{t-1} = S f_{t-2},
+// with S the pull (stencil st on the forward state, maps.m[0]) and S^T the
+// pull with the reflected stencil st2 on mu_t (maps.m[1]).  With st2 the
+// identity the kernel gives the first step of the sweep, Jc^T lambda; with
+// mode 2 it only applies st2 (the last step, S^T mu_1).
+template <int D, int P, typename S, int QM, int N>
+__global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
+    sl_adj_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
+                  const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
+                  const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st2,
+                  const __grid_constant__ TmaMaps maps, const __grid_constant__ WgSchedule sched) {
+  wg_body<D, P, S, false, QM, N, true>(a, vt, st, st2, maps, sched);
+}
+
+template <int D, int P, typename S, int QM, int N>
+int launch_adj(const StepLaunch& Lc) {
+  using C = typename Store<S>::C;
+  using Lay = GLayout<D, P, S>;
+  auto kern = sl_adj_kernel<D, P, S, QM, N>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES);
+    if (e != cudaSuccess) return (int)e;
+    attr_done = true;
+  }
+  const auto& vt = *static_cast<const VelTab<C>*>(Lc.veltab);
+  const auto& st = *static_cast<const StencilTab<C, P + 1>*>(Lc.stentab);
+  const auto& st2 = *static_cast<const StencilTab<C, P + 1>*>(Lc.stentab2);
+  kern<<<Lc.grid, Lay::NT, Lay::BYTES, static_cast<cudaStream_t>(Lc.stream)>>>(Lc.a, vt, st, st2, *Lc.maps,
+                                                                               *Lc.sched);
+  return (int)cudaGetLastError();
 }
 
 template <int D, int P, typename S, bool COMP, int QM, int N>

@@ -115,3 +115,28 @@ def random_fields(shape_zyx, dim, seed, u_amp=0.05, rho_amp=0.02, theta_amp=0.0)
     u = u_amp * (2.0 * rng.random((dim,) + tuple(shape_zyx)) - 1.0)
     theta = 1.0 + theta_amp * (2.0 * rng.random(shape_zyx) - 1.0)
     return rho, u, theta
+
+
+def solenoidal(n, rng, rms, kmin=1, kmax=4):
+    """Divergence-free random velocity on an n^3 periodic grid, array (3, n, n, n).
+
+    The curl of a random vector potential whose Fourier modes have integer
+    wavenumbers with kmin <= |k| <= kmax and Gaussian amplitudes, scaled to
+    the given root-mean-square speed.  ``rng`` is a numpy Generator, so a
+    sequence of fields can be drawn from one seeded stream.
+    """
+    k1 = np.fft.fftfreq(n, 1.0 / n)
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    band = (kk >= kmin) & (kk <= kmax)
+    A = []
+    for _ in range(3):
+        spec = (rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))) * band
+        A.append(np.real(np.fft.ifftn(spec)))
+    Ah = [np.fft.fftn(a) for a in A]  # components x, y, z
+    ik = [1j * kx, 1j * ky, 1j * kz]
+    ux = np.real(np.fft.ifftn(ik[1] * Ah[2] - ik[2] * Ah[1]))
+    uy = np.real(np.fft.ifftn(ik[2] * Ah[0] - ik[0] * Ah[2]))
+    uz = np.real(np.fft.ifftn(ik[0] * Ah[1] - ik[1] * Ah[0]))
+    u = np.stack([ux, uy, uz])
+    return u * (rms / math.sqrt((u ** 2).sum(axis=0).mean()))

@@ -68,6 +68,12 @@ def lib():
             "olb_set_state": (i, [vp, vp, sz, i]),
             "olb_synchronize": (i, [vp, i]),
             "olb_state_sums_noalloc": (i, [i, ctypes.POINTER(Grid), i, d, d, vp, vp, vp]),
+            "olb_tape_reserve": (i, [vp, i]),
+            "olb_tape_record": (i, [vp, i]),
+            "olb_tape_adjoint": (i, [vp, vp, i, i]),
+            "olb_adjoint_step": (i, [vp, vp, vp, i]),
+            "olb_moments_vjp": (i, [vp, vp, vp, vp, i]),
+            "olb_equilibrium_vjp": (i, [vp, vp, vp, vp, vp, vp, i]),
             "olb_strerror": (ctypes.c_char_p, [i]),
             "olb_last_error": (ctypes.c_char_p, []),
         }
@@ -164,6 +170,7 @@ class Sim:
                            ctypes.byref(eb)))
         self.Q, self.planes, self.nodes, self.dim, self.elem_bytes = Q.value, planes.value, nodes.value, dim.value, eb.value
         self.interp_order = int(interp_order)
+        self.storage = storage
         self.stream = stream
 
     # -- lifetime ----------------------------------------------------------
@@ -246,3 +253,46 @@ class Sim:
 
     def synchronize(self, timeout_ms=0):
         _check(lib().olb_synchronize(self._h, int(timeout_ms)))
+
+    # -- adjoint of the isothermal step ----------------------------------------
+    @property
+    def adjoint_dtype(self):
+        """Element type of adjoint arrays: 'float64' for FP64 storage, 'float32' for FP32."""
+        return "float64" if self.storage == "fp64" else "float32"
+
+    def tape_reserve(self, nslots):
+        _check(lib().olb_tape_reserve(self._h, int(nslots)))
+
+    def tape_record(self, n):
+        _check(lib().olb_tape_record(self._h, int(n)))
+
+    def tape_adjoint(self, lam, n):
+        """lam (Q, *grid) in: dJ/d(state after the last recorded step); out: n steps earlier."""
+        p, d = _ptr(lam)
+        _check(lib().olb_tape_adjoint(self._h, p, int(n), d))
+        return lam
+
+    def adjoint_step(self, fwd_state, lam):
+        ps, ds = _ptr(fwd_state)
+        pl, dl = _ptr(lam)
+        if ds != dl:
+            raise ValueError("state and adjoint must both be on the device or both on the host")
+        _check(lib().olb_adjoint_step(self._h, ps, pl, dl))
+        return lam
+
+    def moments_vjp(self, grad_rho, grad_u, lam):
+        pr, dr = _ptr(grad_rho)
+        pu, du = _ptr(grad_u)
+        pl, dl = _ptr(lam)
+        for a, d in ((grad_rho, dr), (grad_u, du)):
+            if a is not None and d != dl:
+                raise ValueError("gradients and adjoint must all be on the device or all on the host")
+        _check(lib().olb_moments_vjp(self._h, pr, pu, pl, dl))
+        return lam
+
+    def equilibrium_vjp(self, rho, u, lam, grad_rho, grad_u):
+        ptrs = [_ptr(a) for a in (rho, u, lam, grad_rho, grad_u)]
+        if len({d for _, d in ptrs}) != 1:
+            raise ValueError("arrays must all be on the device or all on the host")
+        _check(lib().olb_equilibrium_vjp(self._h, *[p for p, _ in ptrs], ptrs[0][1]))
+        return grad_rho, grad_u
