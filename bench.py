@@ -211,10 +211,74 @@ def per_set_table(torch, flush):
     return rows
 
 
+def adjoint_table(torch):
+    """Adjoint of the isothermal step against the forward step (CUDA events).
+
+    D3Q27, N = 2, p = 3, Re = 400, Ma = 0.1 (the adjoint workload) at 64^3
+    (FP32, FP64) and 128^3 (FP32).  Per step: forward (olb_step), recording
+    onto the device tape (olb_tape_record), and the adjoint sweep
+    (olb_tape_adjoint over the recorded segment, scatter and gather of the
+    adjoint included, amortised over the segment).  At 64^3 a state fits in
+    L2, so both sides run partly from L2.
+    """
+    from paper_2101_03982_gb300 import inputs, olb, params
+    rows = []
+    for n, storage in ((64, "fp32"), (64, "fp64"), (128, "fp32")):
+        rp = params.tgv_isothermal("D3Q27", n, 400.0, 0.1, 0.4)
+        sim = olb.Sim((n,) * 3, rp.dx, "D3Q27", 2, rp.tau, rp.dt, interp_order=3, storage=storage,
+                      cs_scale=rp.cs_scale, log_every=1000000)
+        rho, u = inputs.tgv3d(n, rp.u0, rp.cs ** 2)
+        sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        K = 25
+        sim.tape_reserve(K + 1)
+        lam = torch.randn((sim.Q, n, n, n), dtype=getattr(torch, sim.adjoint_dtype), device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def timed(fn, reps=3):
+            fn()
+            best = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                best.append(a.elapsed_time(b) * 1e-3)
+            return statistics.median(best)
+
+        t_fwd = timed(lambda: sim.step(K)) / K
+        t_rec = timed(lambda: sim.tape_record(K)) / K
+        t_adj = timed(lambda: sim.tape_adjoint(lam, K)) / K
+        rows.append(dict(grid=[n] * 3, velocity_set="D3Q27", N=2, p=3, storage=storage, segment=K,
+                         forward_ms=round(t_fwd * 1e3, 4), record_ms=round(t_rec * 1e3, 4),
+                         adjoint_ms=round(t_adj * 1e3, 4), adjoint_over_forward=round(t_adj / t_fwd, 3),
+                         adjoint_plus_recompute_over_forward=round((t_adj + t_rec) / t_fwd, 3),
+                         adjoint_mlups=round(n ** 3 / t_adj / 1e6, 1)))
+        sim.close()
+        del sim, lam
+        torch.cuda.empty_cache()
+    return rows
+
+
+def diagnostics_timing(torch):
+    """Enstrophy diagnostic (off the per-step path) on the default workload."""
+    sim, nodes = make_sim(WORKLOAD, torch)
+    sim.enstrophy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        e = sim.enstrophy()
+    dt = (time.perf_counter() - t0) / reps
+    sim.close()
+    return dict(enstrophy_ms=round(dt * 1e3, 3), enstrophy=e, note="host-timed call incl. read-back")
+
+
 def e2e_measure(w, torch, steps=8):
     """Through the C ABI with host buffers: upload the state from pinned host
-    memory, one step, read back the kinetic energy (device -> host)."""
-    sim, nodes = make_sim(w, torch)
+    memory, one step, read back the kinetic energy (device -> host).  The
+    handle sums k in the step itself (log_every = 1)."""
+    sim, nodes = make_sim(dict(w, log_every=1), torch)
     nb = sim.state_bytes()
     host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
     sim.get_state(host.numpy())
@@ -353,6 +417,8 @@ def main():
 
     e2e = e2e_measure(w, torch)
     per_set = [] if args.no_per_set else per_set_table(torch, flush)
+    adjoint = [] if args.no_per_set else adjoint_table(torch)
+    diagnostics = None if args.no_per_set else diagnostics_timing(torch)
     cpu = None
     if not args.no_cpu:
         prm, f = oracle_setup(w)
@@ -379,6 +445,8 @@ def main():
         "clocks": clk.summary(),
         "k_final": k,
         "per_set": per_set,
+        "adjoint": adjoint,
+        "diagnostics": diagnostics,
     }
     print(json.dumps(line), flush=True)
     if dist:

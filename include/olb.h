@@ -161,6 +161,13 @@ int olb_reductions(olb_handle h, double out[8]);
 /* k and (nullable) the dissipation estimate; a view of olb_reductions(). */
 int olb_kinetic_energy(olb_handle h, double* k, double* dissipation);
 
+/* Enstrophy of the current state (Sec. 4.2): E = mean over the nodes of |curl u|^2, with u from
+ * the moments of the stored populations and fourth-order central differences of spacing dx on
+ * the periodic grid (2D: the z component only).  The scaled enstrophy is nu * E.  Off the
+ * per-step path (three launches and a read-back); synchronises the handle's stream.
+ * OLB_ENONFINITE if the result is not finite. */
+int olb_enstrophy(olb_handle h, double* enstrophy);
+
 /* Populations as FP64 unshifted values, [planes][n]. */
 int olb_get_populations(olb_handle h, double* f, int on_device);
 int olb_set_populations(olb_handle h, const double* f, int on_device);

@@ -251,6 +251,55 @@ __global__ void __launch_bounds__(AUX_NT) equilibrium_vjp_kernel(const __grid_co
   }
 }
 
+// Enstrophy of the velocity field u ([D][n], FP64), Sec. 4.2: the mean of
+// |curl u|^2 with fourth-order central differences on the periodic grid,
+//   d/dx g ~ (g(x-2) - 8 g(x-1) + 8 g(x+1) - g(x+2)) / (12 dx).
+// Per-block FP64 partials in slot 0 of NRED (the other slots are zero).
+__device__ __forceinline__ double d4(const double* g, const Padded& P, int x, int y, int z, int axis, double inv12dx) {
+  int c[3] = {x, y, z};
+  double v[4];
+  const int sh[4] = {-2, -1, 1, 2};
+  for (int k = 0; k < 4; ++k) {
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[axis] = (cc[axis] + sh[k] + 2 * P.n[axis]) % P.n[axis];
+    v[k] = g[((long long)cc[2] * P.n[1] + cc[1]) * P.n[0] + cc[0]];
+  }
+  return (v[0] - 8.0 * v[1] + 8.0 * v[2] - v[3]) * inv12dx;
+}
+
+__global__ void __launch_bounds__(AUX_NT) enstrophy_kernel(const __grid_constant__ AuxArgs a, const double* u,
+                                                        double inv12dx, double* partials) {
+  const long long n = a.nnodes;
+  const double* ux = u;
+  const double* uy = u + n;
+  const double* uz = a.D == 3 ? u + 2 * n : nullptr;
+  double acc = 0.0;
+  for (long long node = blockIdx.x * (long long)AUX_NT + threadIdx.x; node < n;
+       node += (long long)gridDim.x * AUX_NT) {
+    int x, y, z;
+    node_xyz(a.pad, node, x, y, z);
+    const double wz = d4(uy, a.pad, x, y, z, 0, inv12dx) - d4(ux, a.pad, x, y, z, 1, inv12dx);
+    double w2 = wz * wz;
+    if (a.D == 3) {
+      const double wx = d4(uz, a.pad, x, y, z, 1, inv12dx) - d4(uy, a.pad, x, y, z, 2, inv12dx);
+      const double wy = d4(ux, a.pad, x, y, z, 2, inv12dx) - d4(uz, a.pad, x, y, z, 0, inv12dx);
+      w2 += wx * wx + wy * wy;
+    }
+    acc += w2;
+  }
+  __shared__ double sm[AUX_NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) sm[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    double s = 0.0;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < AUX_NT / 32; ++w) s += sm[w];
+    partials[(size_t)blockIdx.x * NRED + threadIdx.x] = s;
+  }
+}
+
 __global__ void __launch_bounds__(256) reduce_final_kernel(const double* partials, int nslots, double* out) {
   __shared__ double sm[256];
   for (int q = 0; q < NRED; ++q) {
@@ -366,6 +415,11 @@ int launch_equilibrium_vjp(const AuxArgs& a, const double* rho, const double* u,
   } else {
     return -1;
   }
+  return (int)cudaGetLastError();
+}
+
+int launch_enstrophy(const AuxArgs& a, const double* u, double dx, double* partials, int grid, void* stream) {
+  enstrophy_kernel<<<grid, AUX_NT, 0, (cudaStream_t)stream>>>(a, u, 1.0 / (12.0 * dx), partials);
   return (int)cudaGetLastError();
 }
 

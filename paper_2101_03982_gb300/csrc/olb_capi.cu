@@ -75,6 +75,9 @@ struct olb_ctx {
   std::vector<unsigned char> st_refl, st_id;  // reflected and identity stencils
   WgSchedule sched_adj[3]{};       // first step, middle steps, last (pull only)
   int adj_ready = 0;
+  // enstrophy diagnostic: velocity field and per-block partials
+  double* ens_u = nullptr;
+  double* ens_part = nullptr;
 };
 
 namespace {
@@ -198,6 +201,8 @@ void release(olb_ctx* h) {
   for (int k = 0; k < 2; ++k)
     if (h->adj[k]) cudaFree(h->adj[k]);
   if (h->adj_scratch) cudaFree(h->adj_scratch);
+  if (h->ens_u) cudaFree(h->ens_u);
+  if (h->ens_part) cudaFree(h->ens_part);
   delete h;
 }
 
@@ -931,6 +936,33 @@ int olb_reductions(olb_handle h, double out[8]) {
   out[2] = from_step ? out[2] / nn : NAN;
   out[3] += h->aux.rho_ref * nn;
   if (out[7] > 0.0) return fail(OLB_ENONFINITE, "state holds non-finite values");
+  return OLB_OK;
+}
+
+int olb_enstrophy(olb_handle h, double* enstrophy) {
+  if (!h || !enstrophy) return fail(OLB_EINVAL, "null handle or output");
+  int rc = set_device(h);
+  if (rc) return rc;
+  const int slots = 1024;
+  if (!h->ens_u) {
+    cudaError_t e = cudaMalloc((void**)&h->ens_u, (size_t)h->nnodes * h->D * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->ens_part, (size_t)slots * NRED * sizeof(double));
+    if (e != cudaSuccess) return fail(OLB_ENOMEM, "enstrophy buffers: " + std::string(cudaGetErrorString(e)));
+  }
+  rc = launch_rc(launch_state_moments(h->aux, h->buf[h->cur], nullptr, h->ens_u, nullptr, nullptr, slots, h->stream),
+                 "state_moments");
+  if (rc) return rc;
+  rc = launch_rc(launch_enstrophy(h->aux, h->ens_u, h->grid.dx, h->ens_part, slots, h->stream), "enstrophy");
+  if (rc) return rc;
+  rc = launch_rc(launch_reduce_final(h->ens_part, slots, h->red_dev, h->stream), "reduce_final");
+  if (rc) return rc;
+  double out[NRED];
+  rc = copy_out(h, out, h->red_dev, NRED * sizeof(double), 0);
+  if (rc) return rc;
+  rc = check_err(h);
+  if (rc) return rc;
+  *enstrophy = out[0] / (double)h->nnodes;
+  if (!std::isfinite(*enstrophy)) return fail(OLB_ENONFINITE, "velocity field holds non-finite values");
   return OLB_OK;
 }
 

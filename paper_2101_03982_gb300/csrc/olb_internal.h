@@ -181,6 +181,9 @@ int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream
 int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream);
 int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream);
 int launch_reduce_final(const double* partials, int nslots, double* out, void* stream);
+// Per-block partial sums of |curl u|^2 (slot 0 of NRED per block) of the
+// velocity u [D][n] (FP64), fourth-order central differences of spacing dx.
+int launch_enstrophy(const AuxArgs& a, const double* u, double dx, double* partials, int grid, void* stream);
 // Adjoint seed and initial-state gradients (FP64 and FP32 storage; -1 otherwise).
 // lam is compact [Q][z][y][x] in the adjoint type (double / float).
 int launch_moments_vjp(const AuxArgs& a, const void* state, const double* grad_rho, const double* grad_u, void* lam,

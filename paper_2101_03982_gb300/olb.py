@@ -68,6 +68,7 @@ def lib():
             "olb_set_state": (i, [vp, vp, sz, i]),
             "olb_synchronize": (i, [vp, i]),
             "olb_state_sums_noalloc": (i, [i, ctypes.POINTER(Grid), i, d, d, vp, vp, vp]),
+            "olb_enstrophy": (i, [vp, dp]),
             "olb_tape_reserve": (i, [vp, i]),
             "olb_tape_record": (i, [vp, i]),
             "olb_tape_adjoint": (i, [vp, vp, i, i]),
@@ -222,6 +223,12 @@ class Sim:
         k, e = ctypes.c_double(), ctypes.c_double()
         _check(lib().olb_kinetic_energy(self._h, ctypes.byref(k), ctypes.byref(e)))
         return k.value, e.value
+
+    def enstrophy(self):
+        """Mean |curl u|^2 of the current state (fourth-order central differences)."""
+        e = ctypes.c_double()
+        _check(lib().olb_enstrophy(self._h, ctypes.byref(e)))
+        return e.value
 
     def get_populations(self, out):
         p, d = _ptr(out)

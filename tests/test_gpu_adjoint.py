@@ -155,7 +155,8 @@ def tgv_sim(olb, n, storage):
     """D3Q27, N = 2, p = 3, Re = 400, Ma = 0.1, Courant 0.4 (the adjoint workload's parameters)."""
     from paper_2101_03982_gb300 import params
     rp = params.tgv_isothermal("D3Q27", n, 400.0, 0.1, 0.4)
-    return olb.Sim((n, n, n), rp.dx, "D3Q27", 2, rp.tau, rp.dt, interp_order=3, storage=storage), rp
+    return olb.Sim((n, n, n), rp.dx, "D3Q27", 2, rp.tau, rp.dt, interp_order=3, storage=storage,
+                   cs_scale=rp.cs_scale), rp
 
 
 def initial_fields(n, rng, rms):
@@ -222,7 +223,7 @@ def test_simfunction_gradient_matches_cpu_adjoint(olb):
     sim, rp = tgv_sim(olb, n, "fp64")
     _, grad = run_J(sim, rho0, u0, nsteps, every, k_final)
     # CPU FP64 adjoint: oracle forward trajectory, seed, sweep, equilibrium link
-    vs = V.get("D3Q27")
+    vs = V.get("D3Q27").scaled(rp.cs_scale)
     prm = O.Params(vs, 2, 3, dt=rp.dt, dx=rp.dx, tau=rp.tau)
     f0, _ = O.init_equilibrium(prm, rho0, u0)
     fT = f0
