@@ -147,6 +147,7 @@ void fill_veltab(olb_ctx* h) {
       r += xh[a] * xh[a];
     }
     t->w[i] = (C)h->set.w[i];
+    t->wt[i] = (C)(h->set.w[i] / h->tau);
     t->xi2[i] = (C)x2;
     t->rD[i] = (C)(r - D);
     t->rpoly[i] = (C)(r * r - 2.0 * (D + 2) * r + D * (D + 2.0));

@@ -59,6 +59,7 @@ struct VelTab {
   C rD[MAXQ];      // |xi/c_s|^2 - D
   C rpoly[MAXQ];   // r^2 - 2 (D+2) r + D (D+2), r = |xi/c_s|^2
   C xx[MAXQ][6];   // xi_a xi_b: xx, yy, zz, xy, xz, yz (2D: xx, yy, 0, xy, 0, 0)
+  C wt[MAXQ];      // w / tau (isothermal)
 };
 
 // Fixed separable stencil of the pull: first support point and Lagrange

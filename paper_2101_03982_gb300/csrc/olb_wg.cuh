@@ -41,13 +41,18 @@ struct GLayout {
   using B = Layout<D, P, S>;
   static constexpr int TX = B::TX, TY = B::TY, TZ = B::TZ, TILE = B::TILE, VEC = B::VEC;
   static constexpr int BXW = B::BXW, NQX = B::NQX, BY = B::BY, BZ = B::BZ;
-  static constexpr int ZCH = 2, YCH = 2;
+  // outputs per thread of the z and y passes (a column of the box; the inputs
+  // slide through a window of P + 1 rows, each loaded once)
+  static constexpr int ZC = TZ, YC = TY < 8 ? TY : 8;
   static constexpr size_t BOXB = B::BOXB;
   static constexpr size_t ABYTES = (size_t)roundup((D == 3 ? TZ * BY * BXW : 4) * (int)sizeof(C), 128);
   static constexpr size_t BBYTES = (size_t)roundup(TZ * TY * BXW * (int)sizeof(C), 128);
   static constexpr size_t WGB = BOXB + ABYTES + BBYTES;  // shared memory of one warpgroup
   static constexpr size_t BUDGET = 227 * 1024 - 2048;
-  static constexpr int NWG = (int)(BUDGET / WGB) >= 4 ? 4 : (int)(BUDGET / WGB);
+  // warpgroups per CTA (at most NWG_MAX); CTAS resident CTAs per SM share the 16 warps
+  static constexpr int NWG_MAX = 4;
+  static constexpr int NWG = (int)(BUDGET / WGB) >= NWG_MAX ? NWG_MAX : (int)(BUDGET / WGB);
+  static constexpr int CTAS = NWG_MAX == 4 ? 1 : 4 / NWG_MAX;
   static constexpr int NT = NWG * WGT;
   static constexpr size_t OFF_R = NWG * WGB;
   static constexpr size_t OFF_M = OFF_R + (NT / 32) * NRED * sizeof(double);
@@ -90,6 +95,25 @@ struct Pr<double> {
   static __device__ __forceinline__ T fma(T a, T b, T c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
   static __device__ __forceinline__ T mul(T a, T b) { return make_double2(a.x * b.x, a.y * b.y); }
 };
+
+// Pairs of FP32 values (two neighbouring nodes) with the paired FP32 pipe.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Two neighbouring values of a plane of the state (8- or 4-byte aligned).
+__device__ __forceinline__ void store_pair(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void store_pair(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void store_pair(double* p, float a, float b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void store_pair(__half* p, float a, float b) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
 
 // A 4-node x group as two pairs.
 template <typename SRC, typename T>
@@ -232,6 +256,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   using L = GLayout<D, P, S>;
   using C = typename Store<S>::C;
   using PR = Pr<C>;
+  // phase B on node pairs with the paired FP32 pipe (isothermal, FP32 arithmetic, up to 27 velocities)
+  constexpr bool PAIRS = !ADJ && !COMP && std::is_same<C, float>::value && QM <= 27;
   using T2 = typename PR::T;
   constexpr int NT = L::NT;
   extern __shared__ unsigned char smem_raw[];
@@ -330,25 +356,27 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 #pragma unroll
         for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][2][j]);
         const int BYA = yact ? L::BY : L::TY;
-        const int items = L::NQX * BYA * (L::TZ / L::ZCH);
         const int PLs = BYA * L::BXW;
-        for (int item = wt; item < items; item += WGT) {
-          const int q = item % L::NQX, r = item / L::NQX, y = r % BYA, zc = r / BYA;
-          const int off = (zc * L::ZCH * BYA + y) * L::BXW + 4 * q;
-          T2 v[L::ZCH + P][2];
+        const int ncol = L::NQX * BYA;
+        for (int col = wt; col < ncol; col += WGT) {
+          const int q = col % L::NQX, y = col / L::NQX;
+          const S* src = box + y * L::BXW + 4 * q;
+          C* out = bufA + y * L::BXW + 4 * q;
+          T2 win[P + 1][2];
 #pragma unroll
-          for (int kk = 0; kk < L::ZCH + P; ++kk) ld4p(box + off + kk * PLs, v[kk][0], v[kk][1]);
+          for (int k = 0; k < P; ++k) ld4p(src + k * PLs, win[k][0], win[k][1]);
 #pragma unroll
-          for (int z = 0; z < L::ZCH; ++z) {
+          for (int z = 0; z < L::ZC; ++z) {
+            ld4p(src + (z + P) * PLs, win[(z + P) % (P + 1)][0], win[(z + P) % (P + 1)][1]);
             T2 o[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              T2 acc = PR::mul(W[0], v[z][h]);
+              T2 acc = PR::mul(W[0], win[z % (P + 1)][h]);
 #pragma unroll
-              for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], v[z + kk][h], acc);
+              for (int k = 1; k <= P; ++k) acc = PR::fma(W[k], win[(z + k) % (P + 1)][h], acc);
               o[h] = acc;
             }
-            st4p(bufA + off + z * PLs, o[0], o[1]);
+            st4p(out + z * PLs, o[0], o[1]);
           }
         }
         wg_barrier(wg);
@@ -358,31 +386,31 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         T2 W[P + 1];
 #pragma unroll
         for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][1][j]);
-        constexpr int NYC = L::TY / L::YCH;
+        constexpr int NYC = L::TY / L::YC;
         constexpr int items = L::NQX * L::TZ * NYC;
         for (int item = wt; item < items; item += WGT) {
           const int q = item % L::NQX, r = item / L::NQX, yc = r % NYC, z = r / NYC;
-          const int off = (z * L::BY + yc * L::YCH) * L::BXW + 4 * q;
-          T2 v[L::YCH + P][2];
-          if (zact) {
+          const int off = (z * L::BY + yc * L::YC) * L::BXW + 4 * q;
+          C* out = bufB + (z * L::TY + yc * L::YC) * L::BXW + 4 * q;
+          T2 win[P + 1][2];
+          auto load = [&](int k, T2& lo, T2& hi) {
+            if (zact) ld4p(bufA + off + k * L::BXW, lo, hi);
+            else ld4p(box + off + k * L::BXW, lo, hi);
+          };
 #pragma unroll
-            for (int kk = 0; kk < L::YCH + P; ++kk) ld4p(bufA + off + kk * L::BXW, v[kk][0], v[kk][1]);
-          } else {
+          for (int k = 0; k < P; ++k) load(k, win[k][0], win[k][1]);
 #pragma unroll
-            for (int kk = 0; kk < L::YCH + P; ++kk) ld4p(box + off + kk * L::BXW, v[kk][0], v[kk][1]);
-          }
-          C* o = bufB + (z * L::TY + yc * L::YCH) * L::BXW + 4 * q;
-#pragma unroll
-          for (int y = 0; y < L::YCH; ++y) {
-            T2 w2[2];
+          for (int y = 0; y < L::YC; ++y) {
+            load(y + P, win[(y + P) % (P + 1)][0], win[(y + P) % (P + 1)][1]);
+            T2 o[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              T2 acc = PR::mul(W[0], v[y][h]);
+              T2 acc = PR::mul(W[0], win[y % (P + 1)][h]);
 #pragma unroll
-              for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], v[y + kk][h], acc);
-              w2[h] = acc;
+              for (int k = 1; k <= P; ++k) acc = PR::fma(W[k], win[(y + k) % (P + 1)][h], acc);
+              o[h] = acc;
             }
-            st4p(o + y * L::BXW, w2[0], w2[1]);
+            st4p(out + y * L::BXW, o[0], o[1]);
           }
         }
         wg_barrier(wg);
@@ -538,6 +566,84 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
     };
 
+    // Two neighbouring nodes (n, n + 1) of one x row per thread, FP32
+    // isothermal sets up to 27 velocities: the paired FP32 pipe does both.
+    // With c = A - rho q/2 [+ rho q^2/8], c1 = rho [- rho q/2], c2 = rho/2
+    // [- rho q/4], c3 = [rho/6], c4 = [rho/24] (brackets: N >= 3, N >= 4),
+    // A + rho Phi = c + s (c1 + s (c2 + s (c3 + s c4))), and the BGK update is
+    // f_post = (1 - 1/tau) f + (w/tau)(A + rho Phi).
+    auto collide2 = [&](int n) {
+      const int lx = n % L::TX, ly = (n / L::TX) % L::TY, lz = n / (L::TX * L::TY);
+      const int x = tx * L::TX + lx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
+      if (x >= pd.n[0] || y >= pd.n[1] || z >= pd.n[2]) return;
+      const bool in1 = x + 1 < pd.n[0];
+      float2 f[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i)
+        f[i] = i < Q ? *reinterpret_cast<const float2*>(scr + (size_t)i * L::TILE + n) : f2(0.f);
+      float2 A = f2(0.f), jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        A = add2(A, f[i]);
+        jx = fma2(f2(vt.xi[i][0]), f[i], jx);
+        jy = fma2(f2(vt.xi[i][1]), f[i], jy);
+        if (D == 3) jz = fma2(f2(vt.xi[i][2]), f[i], jz);
+      }
+      const float2 rho = add2(f2(sc.rho_ref), A);
+      const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
+      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
+      const float2 r2 = mul2(f2(0.5f), rho);
+      float2 c = fma2(f2(-1.f), mul2(r2, q), A);
+      float2 c1 = rho, c2 = r2, c3 = f2(0.f), c4 = f2(0.f);
+      if (N >= 3) {
+        c1 = fma2(f2(-1.f), mul2(r2, q), rho);
+        c3 = mul2(f2(1.0f / 6.0f), rho);
+      }
+      if (N >= 4) {
+        c = fma2(mul2(f2(0.125f), rho), mul2(q, q), c);
+        c2 = fma2(f2(-0.5f), mul2(r2, q), r2);
+        c4 = mul2(f2(1.0f / 24.0f), rho);
+      }
+      const float2 om = f2(1.f - sc.inv_tau);
+      const Images im = images_of(x, y, z);
+      const long long off = pad_index(pd, x, y, z);
+      S* pf = dst + off;
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        float2 s = mul2(f2(vt.xih[i][0]), uhx);
+        s = fma2(f2(vt.xih[i][1]), uhy, s);
+        if (D == 3) s = fma2(f2(vt.xih[i][2]), uhz, s);
+        float2 t = c2;
+        if (N >= 4) t = fma2(fma2(c4, s, c3), s, c2);
+        else if (N >= 3) t = fma2(c3, s, c2);
+        const float2 e = fma2(fma2(t, s, c1), s, c);  // A + rho Phi
+        const float2 o = fma2(om, f[i], mul2(f2(vt.wt[i]), e));
+        if (simple) {
+          store_pair(pf, o.x, o.y);
+          if (im.n) {
+            store_pair(pf + im.i0, o.x, o.y);
+            if (im.n > 1) {
+              store_pair(pf + im.i1, o.x, o.y);
+              store_pair(pf + im.i2, o.x, o.y);
+              if (im.n > 3) {
+                store_pair(pf + im.i3, o.x, o.y);
+                store_pair(pf + im.i4, o.x, o.y);
+                store_pair(pf + im.i5, o.x, o.y);
+                store_pair(pf + im.i6, o.x, o.y);
+              }
+            }
+          }
+        } else {
+          store_all_images(pf - off, pd, x, y, z, Store<S>::st(o.x));
+          if (in1) store_all_images(pf - off, pd, x + 1, y, z, Store<S>::st(o.y));
+        }
+        pf += pd.plane;
+      }
+    };
+
     // adjoint of the collision of one node (isothermal): staged planes
     // q < Q hold the pulled forward populations f~, planes Q + i the pulled
     // adjoint sigma_i.  mu_k = (1 - 1/tau) sigma_k + (a + b . xi^_k) / tau with
@@ -610,6 +716,13 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
     if constexpr (ADJ) {
       for (int n = tid; n < L::TILE; n += NT) adjoint(n);
+    } else if constexpr (PAIRS) {
+      // the logging steps take the one-node path (its sums fit in registers)
+      if (red) {
+        for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, true>());
+      } else {
+        for (int n = 2 * tid; n < L::TILE; n += 2 * NT) collide2(n);
+      }
     } else {
       if (red) {
         for (int n = tid; n < L::TILE; n += NT) collide(n, std::integral_constant<bool, true>());
@@ -646,7 +759,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
 // Forward step (Sec. 3): pull, moments, equilibrium, BGK, global sums.
 template <int D, int P, typename S, bool COMP, int QM, int N>
-__global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
+__global__ void __launch_bounds__(GLayout<D, P, S>::NT, GLayout<D, P, S>::CTAS)
     sl_wg_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
                  const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
                  const __grid_constant__ TmaMaps maps, const __grid_constant__ WgSchedule sched) {
@@ -661,7 +774,7 @@ __global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
 // identity the kernel gives the first step of the sweep, Jc^T lambda; with
 // mode 2 it only applies st2 (the last step, S^T mu_1).
 template <int D, int P, typename S, int QM, int N>
-__global__ void __launch_bounds__(GLayout<D, P, S>::NT, 1)
+__global__ void __launch_bounds__(GLayout<D, P, S>::NT, GLayout<D, P, S>::CTAS)
     sl_adj_kernel(const StepArgs a, const __grid_constant__ VelTab<typename Store<S>::C> vt,
                   const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st,
                   const __grid_constant__ StencilTab<typename Store<S>::C, P + 1> st2,
