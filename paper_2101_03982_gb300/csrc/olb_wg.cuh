@@ -350,6 +350,18 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         if (k2 < nplan) prefetch(tile, sched.plane[wg][k2]);
         else if (tile + (int)gridDim.x < a.ntiles && k2 - nplan < nplan) prefetch(tile + gridDim.x, sched.plane[wg][k2 - nplan]);
       }
+      // the next copy into the box starts as soon as the first pass has read it
+      bool issued = false;
+      auto issue_next = [&]() {
+        issued = true;
+        if (k + 1 < nplan) {
+          if (wt == 0) issue(tile, sched.plane[wg][k + 1]);
+          pending = true;
+        } else if (tile + (int)gridDim.x < a.ntiles) {
+          if (wt == 0) issue(tile + gridDim.x, sched.plane[wg][0]);
+          pending = true;
+        }
+      };
       const C* xsrc_c = nullptr;
       if (zact) {
         T2 W[P + 1];
@@ -380,6 +392,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
           }
         }
         wg_barrier(wg);
+        issue_next();
         xsrc_c = bufA;
       }
       if (yact) {
@@ -414,6 +427,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
           }
         }
         wg_barrier(wg);
+        if (!issued) issue_next();
         xsrc_c = bufB;
       }
       {
@@ -434,14 +448,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
           gst4(scr + (size_t)plane * L::TILE + 4 * qi, out, keep);
         }
       }
-      wg_barrier(wg);  // box and buffers free
-      if (k + 1 < nplan) {
-        if (wt == 0) issue(tile, sched.plane[wg][k + 1]);
-        pending = true;
-      } else if (tile + (int)gridDim.x < a.ntiles) {
-        if (wt == 0) issue(tile + gridDim.x, sched.plane[wg][0]);
-        pending = true;
-      }
+      wg_barrier(wg);  // buffers free
+      if (!issued) issue_next();
     }
     if (__syncthreads_or(failed)) {
       failed = true;
