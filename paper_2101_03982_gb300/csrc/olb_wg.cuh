@@ -47,7 +47,11 @@ struct GLayout {
   static constexpr size_t BOXB = B::BOXB;
   static constexpr size_t ABYTES = (size_t)roundup((D == 3 ? TZ * BY * BXW : 4) * (int)sizeof(C), 128);
   static constexpr size_t BBYTES = (size_t)roundup(TZ * TY * BXW * (int)sizeof(C), 128);
-  static constexpr size_t WGB = BOXB + ABYTES + BBYTES;  // shared memory of one warpgroup
+  // 3D with storage of the arithmetic type: two boxes per warpgroup, the z
+  // and y passes write in place (each column belongs to one thread), the copy
+  // of the next plane but one lands while a plane is processed
+  static constexpr bool INPL = D == 3 && sizeof(S) == sizeof(C);
+  static constexpr size_t WGB = INPL ? 2 * BOXB : BOXB + ABYTES + BBYTES;  // shared memory of one warpgroup
   static constexpr size_t BUDGET = 227 * 1024 - 2048;
   // warpgroups per CTA (at most NWG_MAX); CTAS resident CTAs per SM share the 16 warps
   static constexpr int NWG_MAX = 4;
@@ -56,7 +60,7 @@ struct GLayout {
   static constexpr int NT = NWG * WGT;
   static constexpr size_t OFF_R = NWG * WGB;
   static constexpr size_t OFF_M = OFF_R + (NT / 32) * NRED * sizeof(double);
-  static constexpr size_t BYTES = OFF_M + 4 * sizeof(unsigned long long) + 128;
+  static constexpr size_t BYTES = OFF_M + 2 * NWG * sizeof(unsigned long long) + 128;
   static_assert(NWG >= 1, "one warpgroup must fit");
 };
 
@@ -129,6 +133,44 @@ template <typename C, typename T>
 __device__ __forceinline__ void st4p(C* p, T lo, T hi) {
   const C v[4] = {lo.x, lo.y, hi.x, hi.y};
   st4(p, v);
+}
+
+// x pass of one 4-node group from a row of C values (s: first node's column,
+// rounded down to the 16-byte granule; XO: offset of the first needed value).
+template <int P, int XO, bool XACT, typename C>
+__device__ __forceinline__ void xrow(const C* s, const C* W, C out[4]) {
+  if (!XACT) {
+    ld4(s, out);
+    return;
+  }
+  constexpr int NQ = (XO + 3 + P) / 4 + 1;
+  C v[NQ * 4];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) ld4(s + 4 * k, &v[4 * k]);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    C acc = W[0] * v[XO + e];
+#pragma unroll
+    for (int j = 1; j <= P; ++j) acc = fma(W[j], v[XO + e + j], acc);
+    out[e] = acc;
+  }
+}
+
+template <int P, int VEC, int XO = 0, typename C>
+__device__ __forceinline__ void xrow_any(bool xact, int xo, const C* s, const C* W, C out[4]) {
+  if constexpr (XO == 0) {
+    if (!xact) {
+      xrow<P, 0, false>(s, W, out);
+      return;
+    }
+  }
+  if constexpr (XO < VEC) {
+    if (xo == XO) {
+      xrow<P, XO, true>(s, W, out);
+      return;
+    }
+    xrow_any<P, VEC, XO + 1>(true, xo, s, W, out);
+  }
 }
 
 __device__ __forceinline__ void wg_barrier(int wg) {
@@ -266,10 +308,11 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   const int wg = tid / WGT, wt = tid % WGT;
   unsigned char* mine = base + wg * L::WGB;
   S* box = reinterpret_cast<S*>(mine);
+  S* box1 = reinterpret_cast<S*>(mine + (L::INPL ? L::BOXB : 0));
   C* bufA = reinterpret_cast<C*>(mine + L::BOXB);
   C* bufB = reinterpret_cast<C*>(mine + L::BOXB + L::ABYTES);
   double* red_smem = reinterpret_cast<double*>(base + L::OFF_R);
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base + L::OFF_M) + wg;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base + L::OFF_M) + 2 * wg;
 
   const int Q = a.Q, planes = a.planes;
   const Padded& pd = a.pad;
@@ -295,13 +338,21 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     Z = D == 3 ? (r / a.nt[1]) * L::TZ + pd.gl[2] + ((act & 4) ? T.m0[i][2] : 0) : 0;
     return ((act & 2) ? 1 : 0) | ((D == 3 && (act & 4)) ? 2 : 0);
   };
-  auto issue = [&](int tile, int plane) {
+  auto issue = [&](int tile, int plane, int b = 0) {
     int X, Y, Z;
     const int v = box_coords(tile, plane, X, Y, Z);
     const unsigned bytes = (unsigned)(L::BXW * ((v & 1) ? L::BY : L::TY) * ((v & 2) ? L::BZ : L::TZ) * sizeof(S));
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, bytes);
-    tma_load_4d(box, &maps_of(plane)[v], X, Y, Z, tplane_of(plane), bar);
+    mbar_expect_tx(bar + b, bytes);
+    tma_load_4d(b ? box1 : box, &maps_of(plane)[v], X, Y, Z, tplane_of(plane), bar + b);
+  };
+  // (tile, k) of the plane `steps` after (tile, k) in this warpgroup's stream
+  auto advance = [&](int& t, int& k, int steps) {
+    k += steps;
+    while (k >= nplan) {
+      k -= nplan;
+      t += gridDim.x;
+    }
   };
   auto prefetch = [&](int tile, int plane) {
     int X, Y, Z;
@@ -309,19 +360,32 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     tma_prefetch_4d(&maps_of(plane)[v], X, Y, Z, tplane_of(plane));
   };
 
-  if (wt == 0) mbar_init(bar, 1);
+  if (wt == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+  }
   if (tid < (NT / 32) * NRED) red_smem[tid] = 0.0;
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   __syncthreads();
-  bool pending = false;  // a copy into this warpgroup's box is in flight
+  bool pending = false;   // a copy into box 0 is in flight
+  bool pending1 = false;  // a copy into box 1 is in flight (two-box staging)
   if (nplan > 0 && (int)blockIdx.x < a.ntiles) {
     if (wt == 0) {
       issue(blockIdx.x, sched.plane[wg][0]);
-      if (nplan > 1) prefetch(blockIdx.x, sched.plane[wg][1]);
+      if (!L::INPL && nplan > 1) prefetch(blockIdx.x, sched.plane[wg][1]);
     }
     pending = true;
+    if (L::INPL) {
+      int t1 = blockIdx.x, k1 = 0;
+      advance(t1, k1, 1);
+      if (t1 < a.ntiles) {
+        if (wt == 0) issue(t1, sched.plane[wg][k1], 1);
+        pending1 = true;
+      }
+    }
   }
-  unsigned parity = 0;
+  unsigned parity = 0;  // bit b: phase parity of box b's barrier
+  int cb = 0;           // box of the current plane (two-box staging)
   bool failed = false;
 
   // every axis holds at least one stencil reach on each side: a node has at
@@ -331,6 +395,109 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     // ---------------- phase A: pull every plane of the tile -----------------
+    if constexpr (L::INPL) {
+      for (int k = 0; k < nplan && !failed; ++k) {
+        const int plane = sched.plane[wg][k];
+        if (wg_any(wg, !mbar_wait_bounded(bar + cb, (parity >> cb) & 1u))) {
+          failed = true;
+          break;
+        }
+        parity ^= 1u << cb;
+        if (cb) pending1 = false;
+        else pending = false;
+        const int i = plane < Q ? plane : plane - Q;
+        const auto& T = tab_of(plane);
+        const int act = T.active[i];
+        const bool zact = (act & 4) != 0, yact = (act & 2) != 0, xact = (act & 1) != 0;
+        if (wt == 0) {
+          // warm L2 with the plane after the two in flight
+          int t3 = tile, k3 = k;
+          advance(t3, k3, 3);
+          if (t3 < a.ntiles) prefetch(t3, sched.plane[wg][k3]);
+        }
+        C* bx = reinterpret_cast<C*>(cb ? box1 : box);
+        const int BYA = yact ? L::BY : L::TY;
+        const int PLs = BYA * L::BXW;
+        if (zact) {
+          T2 W[P + 1];
+#pragma unroll
+          for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][2][j]);
+          const int ncol = L::NQX * BYA;
+          for (int col = wt; col < ncol; col += WGT) {
+            const int q = col % L::NQX, y = col / L::NQX;
+            C* c0 = bx + y * L::BXW + 4 * q;
+            T2 win[P + 1][2];
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) ld4p(c0 + kk * PLs, win[kk][0], win[kk][1]);
+#pragma unroll
+            for (int z = 0; z < L::TZ; ++z) {
+              ld4p(c0 + (z + P) * PLs, win[(z + P) % (P + 1)][0], win[(z + P) % (P + 1)][1]);
+              T2 o[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                T2 acc = PR::mul(W[0], win[z % (P + 1)][h]);
+#pragma unroll
+                for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], win[(z + kk) % (P + 1)][h], acc);
+                o[h] = acc;
+              }
+              st4p(c0 + z * PLs, o[0], o[1]);  // row z is no longer read by this column
+            }
+          }
+          wg_barrier(wg);
+        }
+        if (yact) {
+          T2 W[P + 1];
+#pragma unroll
+          for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][1][j]);
+          constexpr int ncol = L::NQX * L::TZ;
+          for (int col = wt; col < ncol; col += WGT) {
+            const int q = col % L::NQX, z = col / L::NQX;
+            C* c0 = bx + z * PLs + 4 * q;
+            T2 win[P + 1][2];
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) ld4p(c0 + kk * L::BXW, win[kk][0], win[kk][1]);
+#pragma unroll
+            for (int y = 0; y < L::TY; ++y) {
+              ld4p(c0 + (y + P) * L::BXW, win[(y + P) % (P + 1)][0], win[(y + P) % (P + 1)][1]);
+              T2 o[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                T2 acc = PR::mul(W[0], win[y % (P + 1)][h]);
+#pragma unroll
+                for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], win[(y + kk) % (P + 1)][h], acc);
+                o[h] = acc;
+              }
+              st4p(c0 + y * L::BXW, o[0], o[1]);
+            }
+          }
+          wg_barrier(wg);
+        }
+        {
+          C W[P + 1];
+#pragma unroll
+          for (int j = 0; j <= P; ++j) W[j] = T.W[i][0][j];
+          const int xo = xact ? ((T.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
+          constexpr int QPT = L::TILE / 4 / WGT;  // 4-node x groups per thread
+#pragma unroll
+          for (int m = 0; m < QPT; ++m) {
+            const int qi = wt + WGT * m;
+            const int qx = (qi % (L::TX / 4)) * 4, ly = (qi / (L::TX / 4)) % L::TY, lz = qi / (L::TX / 4 * L::TY);
+            C out[4];
+            xrow_any<P, L::VEC>(xact, xo, bx + (lz * BYA + ly) * L::BXW + qx, W, out);
+            gst4(scr + (size_t)plane * L::TILE + 4 * qi, out, keep);
+          }
+        }
+        wg_barrier(wg);  // box free
+        int t2 = tile, k2 = k;
+        advance(t2, k2, 2);
+        if (t2 < a.ntiles) {
+          if (wt == 0) issue(t2, sched.plane[wg][k2], cb);
+          if (cb) pending1 = true;
+          else pending = true;
+        }
+        cb ^= 1;
+      }
+    } else
     for (int k = 0; k < nplan && !failed; ++k) {
       const int plane = sched.plane[wg][k];
       // every thread of the warpgroup takes the same decision
@@ -752,7 +919,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
   if (failed) {
     if (tid == 0) atomicExch(a.err, 1);
-    if (wt == 0 && pending) mbar_wait_bounded(bar, parity);  // let the copy in flight land
+    // let the copies in flight land
+    if (wt == 0 && pending) mbar_wait_bounded(bar, parity & 1u);
+    if (wt == 0 && pending1) mbar_wait_bounded(bar + 1, (parity >> 1) & 1u);
     return;
   }
   if (!ADJ && a.reduce) {
