@@ -477,14 +477,29 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 #pragma unroll
           for (int j = 0; j <= P; ++j) W[j] = T.W[i][0][j];
           const int xo = xact ? ((T.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
-          constexpr int QPT = L::TILE / 4 / WGT;  // 4-node x groups per thread
-#pragma unroll
-          for (int m = 0; m < QPT; ++m) {
-            const int qi = wt + WGT * m;
-            const int qx = (qi % (L::TX / 4)) * 4, ly = (qi / (L::TX / 4)) % L::TY, lz = qi / (L::TX / 4 * L::TY);
-            C out[4];
-            xrow_any<P, L::VEC>(xact, xo, bx + (lz * BYA + ly) * L::BXW + qx, W, out);
-            gst4(scr + (size_t)plane * L::TILE + 4 * qi, out, keep);
+          // one alignment variant per plane (dispatched once), rolled over the groups
+          auto groups = [&](auto XOc, auto ACT) {
+            constexpr int QPT = L::TILE / 4 / WGT;  // 4-node x groups per thread
+            C* so = scr + (size_t)plane * L::TILE;
+#pragma unroll 1
+            for (int m = 0; m < QPT; ++m) {
+              const int qi = wt + WGT * m;
+              const int qx = (qi % (L::TX / 4)) * 4, ly = (qi / (L::TX / 4)) % L::TY,
+                        lz = qi / (L::TX / 4 * L::TY);
+              C out[4];
+              xrow<P, decltype(XOc)::value, decltype(ACT)::value>(bx + (lz * BYA + ly) * L::BXW + qx, W, out);
+              gst4(so + 4 * qi, out, keep);
+            }
+          };
+          if (!xact) {
+            groups(std::integral_constant<int, 0>(), std::false_type());
+          } else {
+            switch (xo) {
+              case 0: groups(std::integral_constant<int, 0>(), std::true_type()); break;
+              case 1: groups(std::integral_constant<int, 1>(), std::true_type()); break;
+              case 2: if constexpr (L::VEC > 2) groups(std::integral_constant<int, 2>(), std::true_type()); break;
+              default: if constexpr (L::VEC > 3) groups(std::integral_constant<int, 3>(), std::true_type()); break;
+            }
           }
         }
         wg_barrier(wg);  // box free
@@ -697,28 +712,74 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       const Images im = images_of(x, y, z);
       const long long off = pad_index(pd, x, y, z);
-      // equilibrium (Appendix A), BGK (Sec. 3) and the stores
+      // The closed form of order N (Appendix A) as a polynomial in s = xi^.u^,
+      // Phi - 1 = c0 + s (c1 + s (c2 + s (c3 + s c4))), whose coefficients
+      // depend on the velocity only through r_D = |xi^|^2 - D and
+      // r_P = r^2 - 2 (D + 2) r + D (D + 2):
+      //   c0 = a0 + a1 r_D + a2 r_P,  c1 = b0 + b1 r_D,  c2 = g0 + g1 r_D.
+      C a0 = C(-0.5) * q, a1 = C(0), a2 = C(0), b0 = C(1), b1 = C(0), g0 = C(0.5), g1 = C(0), c3 = C(0),
+        c4 = C(0);
+      if (COMP) a1 = C(0.5) * tt;
+      if (N >= 3) {
+        b0 = b0 - C(0.5) * q - (COMP ? tt : C(0));
+        if (COMP) b1 = C(0.5) * tt;
+        c3 = C(1.0 / 6.0);
+      }
+      if (N >= 4) {
+        a0 = fma(C(0.125) * q, q, a0);
+        g0 = g0 - C(0.25) * q;
+        c4 = C(1.0 / 24.0);
+        if (COMP) {
+          a0 = fma(C(0.5) * tt, q, a0);
+          a1 = fma(C(-0.25) * tt, q, a1);
+          a2 = C(0.125) * tt * tt;
+          g0 = g0 - tt;
+          g1 = C(0.25) * tt;
+        }
+      }
+      auto phi = [&](int i) {
+        C s = vt.xih[i][0] * uhx;
+        s = fma(vt.xih[i][1], uhy, s);
+        if (D == 3) s = fma(vt.xih[i][2], uhz, s);
+        C c0 = a0, c1 = b0, c2 = g0;
+        if (COMP) {
+          c0 = fma(a1, vt.rD[i], c0);
+          if (N >= 4) c0 = fma(a2, vt.rpoly[i], c0);
+          if (N >= 3) c1 = fma(b1, vt.rD[i], c1);
+          if (N >= 4) c2 = fma(g1, vt.rD[i], c2);
+        }
+        C hp = c2;
+        if (N >= 4) hp = fma(fma(c4, s, c3), s, c2);
+        else if (N >= 3) hp = fma(c3, s, c2);
+        return fma(fma(hp, s, c1), s, c0);
+      };
+      // equilibrium (Appendix A), BGK (Sec. 3) and the stores: f first
       S* pf = dst + off;
       C Pi[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
-        C s = vt.xih[i][0] * uhx;
-        s = fma(vt.xih[i][1], uhy, s);
-        if (D == 3) s = fma(vt.xih[i][2], uhz, s);
-        const C ph = phi_n<C, COMP, N>(s, q, tt, vt.rD[i], vt.rpoly[i]);
+        const C ph = phi(i);
         const C feqd = vt.w[i] * fma(rho, ph, A);
         const C fneq = f[i] - feqd;
         im.put(pf, Store<S>::st(fma(-fneq, itau, f[i])), pd, off, x, y, z);
-        if (COMP) {
-          const C gv = scr[(size_t)(Q + i) * L::TILE + n];
-          const C geqd = vt.w[i] * sc.gfac * fma(rth, ph, gA);
-          im.put(pf + (long long)Q * pd.plane, Store<S>::st(fma(-(gv - geqd), itau, gv)), pd, off, x, y, z);
-        }
         pf += pd.plane;
         if (R) {
 #pragma unroll
           for (int c = 0; c < 6; ++c) Pi[c] = fma(vt.xx[i][c], fneq, Pi[c]);
+        }
+      }
+      if (COMP) {
+        // then g: all staged g values loaded at once into the registers f held,
+        // the polynomial evaluated again (cheaper than a load per velocity)
+#pragma unroll
+        for (int i = 0; i < QM; ++i) f[i] = i < Q ? scr[(size_t)(Q + i) * L::TILE + n] : C(0);
+#pragma unroll
+        for (int i = 0; i < QM; ++i) {
+          if (i >= Q) break;
+          const C geqd = vt.w[i] * sc.gfac * fma(rth, phi(i), gA);
+          im.put(pf, Store<S>::st(fma(-(f[i] - geqd), itau, f[i])), pd, off, x, y, z);
+          pf += pd.plane;
         }
       }
       if (R) {
