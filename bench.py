@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
 # default workload, from one ncu capture of the kernel source with this hash
 # (summary in profiles/); reported as null once the kernel source changes.
-TRAFFIC = {"kernel_sha": "eee2429c9889331c", "bytes": 341244416 + 324843520}
+TRAFFIC = {"kernel_sha": "99110e13180d72cf", "bytes": 315065600 + 308365824}
 
 
 def workload_name(w):

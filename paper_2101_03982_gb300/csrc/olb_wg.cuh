@@ -198,28 +198,6 @@ __device__ __forceinline__ int one_image(int c, int n, int reach_lo, int reach_h
   return 0;
 }
 
-// Equilibrium of order N (Appendix A) in closed form, f^eq_i/(w_i rho) - 1.
-template <typename C, bool COMP, int N>
-__device__ __forceinline__ C phi_n(C s, C q, C t, C rD, C rpoly) {
-  const C s2 = s * s;
-  C v = s;
-  {
-    C h = s2 - q;
-    if (COMP) h = fma(t, rD, h);
-    v = fma(C(0.5), h, v);
-  }
-  if (N >= 3) {
-    C h = s * (s2 - C(3) * q);
-    if (COMP) h = fma(C(3) * t * s, rD - C(2), h);
-    v = fma(C(1.0 / 6.0), h, v);
-  }
-  if (N >= 4) {
-    C h = s2 * s2 - C(6) * s2 * q + C(3) * q * q;
-    if (COMP) h += C(6) * t * (s2 * (rD - C(4)) - q * (rD - C(2))) + C(3) * t * t * rpoly;
-    v = fma(C(1.0 / 24.0), h, v);
-  }
-  return v;
-}
 
 // d Phi/ds and d Phi/dq of the isothermal closed form of order N (theta = 1):
 // Phi = s + (s^2 - q)/2 [+ s (s^2 - 3q)/6] [+ (s^4 - 6 s^2 q + 3 q^2)/24].

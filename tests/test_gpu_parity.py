@@ -247,7 +247,7 @@ def test_nonfinite_state_is_reported(olb):
     sim.close()
 
 
-def test_bounded_wait(olb):
+def test_synchronize_with_time_limit(olb):
     sim, _, _ = make_pair(olb, "D3Q27", (32, 16, 16), N=2, p=4)
     sim.step(2)
     sim.synchronize(timeout_ms=60000)
