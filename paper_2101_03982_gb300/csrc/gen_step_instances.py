@@ -68,7 +68,7 @@ def emit(st, D):
     L.append("")
     L.append("// Two-phase instance for (P, comp, Q, N): its launch and shape, or null.")
     L.append("using WgLaunch = int (*)(const StepLaunch&);")
-    L.append("using WgOcc = int (*)(size_t*, int*);")
+    L.append("using WgOcc = int (*)(StepInfo*);")
     L.append("bool pick_wg(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {")
     for (P, comp, qm, N) in wg_cases(D):
         c = "1" if comp else "0"
@@ -102,9 +102,7 @@ def emit(st, D):
         L.append(f"    layout_of<{D}, {P}, S>(out);")
         if P in WG_P:
             L.append("    if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {")
-            L.append("      int nwg = 0;")
-            L.append("      out->ctas_per_sm = o(&out->smem, &nwg);")
-            L.append("      out->wg = nwg;")
+            L.append("      out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape")
             L.append("      return 0;")
             L.append("    }")
         L.append(f"    out->ctas_per_sm = comp ? occupancy_one<{D}, {P}, S, true>(&out->smem)")

@@ -8,7 +8,7 @@ using S = __half;
 
 // Two-phase instance for (P, comp, Q, N): its launch and shape, or null.
 using WgLaunch = int (*)(const StepLaunch&);
-using WgOcc = int (*)(size_t*, int*);
+using WgOcc = int (*)(StepInfo*);
 bool pick_wg(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {
   if (P == 3 && comp == 0 && N == 2 && Q <= 9) {
     *l = wg::launch_wg<2, 3, S, false, 9, 2>;
@@ -90,9 +90,7 @@ int step_info_f16_2d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   if (P == 3) {
     layout_of<2, 3, S>(out);
     if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
-      int nwg = 0;
-      out->ctas_per_sm = o(&out->smem, &nwg);
-      out->wg = nwg;
+      out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;
     }
     out->ctas_per_sm = comp ? occupancy_one<2, 3, S, true>(&out->smem)
@@ -102,9 +100,7 @@ int step_info_f16_2d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   if (P == 4) {
     layout_of<2, 4, S>(out);
     if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
-      int nwg = 0;
-      out->ctas_per_sm = o(&out->smem, &nwg);
-      out->wg = nwg;
+      out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;
     }
     out->ctas_per_sm = comp ? occupancy_one<2, 4, S, true>(&out->smem)

@@ -39,12 +39,14 @@ template <int D, int P, typename S>
 struct GLayout {
   using C = typename Store<S>::C;
   using B = Layout<D, P, S>;
-  static constexpr int TX = B::TX, TY = B::TY, TZ = B::TZ, TILE = B::TILE, VEC = B::VEC;
-  static constexpr int BXW = B::BXW, NQX = B::NQX, BY = B::BY, BZ = B::BZ;
+  // tile of the two-phase kernel: x and y as the single-role kernel, z depth WG_TZ
+  static constexpr int WG_TZ = 8;
+  static constexpr int TX = B::TX, TY = B::TY, TZ = D == 3 ? WG_TZ : 1, TILE = TX * TY * TZ, VEC = B::VEC;
+  static constexpr int BXW = B::BXW, NQX = B::NQX, BY = B::BY, BZ = D == 3 ? TZ + P : 1;
   // outputs per thread of the z and y passes (a column of the box; the inputs
   // slide through a window of P + 1 rows, each loaded once)
   static constexpr int ZC = TZ, YC = TY < 8 ? TY : 8;
-  static constexpr size_t BOXB = B::BOXB;
+  static constexpr size_t BOXB = (size_t)roundup(BZ * BY * BXW * (int)sizeof(S), 128);
   static constexpr size_t ABYTES = (size_t)roundup((D == 3 ? TZ * BY * BXW : 4) * (int)sizeof(C), 128);
   static constexpr size_t BBYTES = (size_t)roundup(TZ * TY * BXW * (int)sizeof(C), 128);
   // 3D with storage of the arithmetic type: two boxes per warpgroup, the z
@@ -1035,11 +1037,19 @@ int launch_wg(const StepLaunch& Lc) {
 }
 
 template <int D, int P, typename S, bool COMP, int QM, int N>
-int occupancy_wg(size_t* smem, int* nwg) {
+int occupancy_wg(StepInfo* o) {
   using Lay = GLayout<D, P, S>;
   auto kern = sl_wg_kernel<D, P, S, COMP, QM, N>;
-  *smem = Lay::BYTES;
-  *nwg = Lay::NWG;
+  o->bxw = Lay::BXW;
+  o->by = Lay::BY;
+  o->bz = Lay::BZ;
+  o->tile = Lay::TILE;
+  o->tx = Lay::TX;
+  o->ty = Lay::TY;
+  o->tz = Lay::TZ;
+  o->vec = Lay::VEC;
+  o->smem = Lay::BYTES;
+  o->wg = Lay::NWG;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES) != cudaSuccess)
     return 0;
   int n = 0;
