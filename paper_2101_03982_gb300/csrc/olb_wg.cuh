@@ -307,15 +307,23 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   auto tab_of = [&](int plane) -> const StencilTab<C, P + 1>& { return (ADJ && plane >= Q) ? st2 : st; };
   auto maps_of = [&](int plane) -> const CUtensorMap* { return (ADJ && plane >= Q) ? maps.m[1] : maps4; };
   auto tplane_of = [&](int plane) { return (ADJ && plane >= Q) ? plane - Q : plane; };
+  // padded-grid origin of a tile, cached (the divisions run once per tile)
+  int org_tile = -1, org[3] = {0, 0, 0};
   auto box_coords = [&](int tile, int plane, int& X, int& Y, int& Z) {
-    const int tx = tile % a.nt[0], r = tile / a.nt[0];
+    if (tile != org_tile) {
+      const int tx = tile % a.nt[0], r = tile / a.nt[0];
+      org[0] = tx * L::TX + pd.gl[0];
+      org[1] = (r % a.nt[1]) * L::TY + pd.gl[1];
+      org[2] = D == 3 ? (r / a.nt[1]) * L::TZ + pd.gl[2] : 0;
+      org_tile = tile;
+    }
     const int i = plane < Q ? plane : plane - Q;
     const auto& T = tab_of(plane);
     const int act = T.active[i];
-    X = tx * L::TX + pd.gl[0] + ((act & 1) ? T.m0[i][0] : 0);
+    X = org[0] + ((act & 1) ? T.m0[i][0] : 0);
     X -= X % L::VEC;
-    Y = (r % a.nt[1]) * L::TY + pd.gl[1] + ((act & 2) ? T.m0[i][1] : 0);
-    Z = D == 3 ? (r / a.nt[1]) * L::TZ + pd.gl[2] + ((act & 4) ? T.m0[i][2] : 0) : 0;
+    Y = org[1] + ((act & 2) ? T.m0[i][1] : 0);
+    Z = D == 3 ? org[2] + ((act & 4) ? T.m0[i][2] : 0) : 0;
     return ((act & 2) ? 1 : 0) | ((D == 3 && (act & 4)) ? 2 : 0);
   };
   auto issue = [&](int tile, int plane, int b = 0) {
@@ -389,12 +397,6 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const auto& T = tab_of(plane);
         const int act = T.active[i];
         const bool zact = (act & 4) != 0, yact = (act & 2) != 0, xact = (act & 1) != 0;
-        if (wt == 0) {
-          // warm L2 with the plane after the two in flight
-          int t3 = tile, k3 = k;
-          advance(t3, k3, 3);
-          if (t3 < a.ntiles) prefetch(t3, sched.plane[wg][k3]);
-        }
         C* bx = reinterpret_cast<C*>(cb ? box1 : box);
         const int BYA = yact ? L::BY : L::TY;
         const int PLs = BYA * L::BXW;
