@@ -644,9 +644,15 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       C f[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) f[i] = i < Q ? scr[(size_t)i * L::TILE + n] : C(0);
-      // moments (Sec. 3)
-      C A = C(0), jx = C(0), jy = C(0), jz = C(0), Bp = C(0);
-      double Bd = 0.0;
+      // moments (Sec. 3).  Compressible energy sums: FP32 groups of eight
+      // merged by error-free additions into (hi, lo) pairs (the FP64 pipe of
+      // this GPU is narrow; the cancellation below is done in FP64).
+      auto merge = [](C& hi, C& lo, C v) {
+        const C t = hi + v, e = t - hi;
+        lo += (hi - (t - e)) + (v - e);
+        hi = t;
+      };
+      C A = C(0), jx = C(0), jy = C(0), jz = C(0), Bp = C(0), Bh = C(0), Bl = C(0);
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
@@ -657,7 +663,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         if (COMP) {
           Bp = fma(vt.xi2[i], f[i], Bp);
           if ((i & 7) == 7) {
-            Bd += (double)Bp;
+            merge(Bh, Bl, Bp);
             Bp = C(0);
           }
         }
@@ -668,23 +674,22 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       const C q = uhx * uhx + uhy * uhy + uhz * uhz;
       C itau = sc.inv_tau, tt = C(0), gA = C(0), rth = C(0), theta = C(1), tau = sc.tau;
       if (COMP) {
-        Bd += (double)Bp;
-        // sum of the pulled g (Sec. 3 temperature relation), FP32 groups into FP64
-        double Gd = 0.0;
-        C Gp = C(0);
+        merge(Bh, Bl, Bp);
+        // sum of the pulled g (Sec. 3 temperature relation), FP32 groups merged exactly
+        C Gp = C(0), Gh = C(0), Gl = C(0);
 #pragma unroll
         for (int i = 0; i < QM; ++i) {
           if (i >= Q) break;
           Gp += scr[(size_t)(Q + i) * L::TILE + n];
           if ((i & 7) == 7) {
-            Gd += (double)Gp;
+            merge(Gh, Gl, Gp);
             Gp = C(0);
           }
         }
-        Gd += (double)Gp;
-        const double r = (double)rho;
-        const double jj = (double)jx * jx + (double)jy * jy + (double)jz * jz;
-        const double X = Bd + Gd - jj / r - (double)sc.two_cv * (double)A;
+        merge(Gh, Gl, Gp);
+        // 2 C_v (rho theta - rho) = B + G - |j|^2/rho - 2 C_v A, cancelling in FP64
+        const C K = (jx * jx + jy * jy + jz * jz) * ir;
+        const double X = fma(-a.two_cv, (double)A, (((double)Bh + (double)Bl) + ((double)Gh + (double)Gl)) - (double)K);
         tt = C(X) / (sc.two_cv * rho);
         theta = C(1) + tt;
         tau = sc.mu_dt / (rho * theta) + C(0.5);
