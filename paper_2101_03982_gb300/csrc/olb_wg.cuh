@@ -280,6 +280,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   using PR = Pr<C>;
   // phase B on node pairs with the paired FP32 pipe (isothermal, FP32 arithmetic, up to 27 velocities)
   constexpr bool PAIRS = !ADJ && !COMP && std::is_same<C, float>::value && QM <= 27;
+  constexpr bool APAIRS = ADJ && std::is_same<C, float>::value && QM <= 27 && N <= 3;
   using T2 = typename PR::T;
   constexpr int NT = L::NT;
   extern __shared__ unsigned char smem_raw[];
@@ -867,6 +868,105 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
     };
 
+    // The adjoint of the collision for two neighbouring nodes per thread on
+    // the paired FP32 pipe (FP32, up to 27 velocities); same arithmetic as
+    // `adjoint` below.
+    auto adjoint2 = [&](int n) {
+      const int lx = n % L::TX, ly = (n / L::TX) % L::TY, lz = n / (L::TX * L::TY);
+      const int x = tx * L::TX + lx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
+      if (x >= pd.n[0] || y >= pd.n[1] || z >= pd.n[2]) return;
+      const bool in1 = x + 1 < pd.n[0];
+      const Images im = images_of(x, y, z);
+      const long long off = pad_index(pd, x, y, z);
+      S* pf = dst + off;
+      const float* sg = reinterpret_cast<const float*>(scr) + (size_t)Q * L::TILE + n;
+      auto put2 = [&](float2 o) {
+        if (simple) {
+          store_pair(pf, o.x, o.y);
+          if (im.n) {
+            store_pair(pf + im.i0, o.x, o.y);
+            if (im.n > 1) {
+              store_pair(pf + im.i1, o.x, o.y);
+              store_pair(pf + im.i2, o.x, o.y);
+              if (im.n > 3) {
+                store_pair(pf + im.i3, o.x, o.y);
+                store_pair(pf + im.i4, o.x, o.y);
+                store_pair(pf + im.i5, o.x, o.y);
+                store_pair(pf + im.i6, o.x, o.y);
+              }
+            }
+          }
+        } else {
+          store_all_images(pf - off, pd, x, y, z, Store<S>::st(o.x));
+          if (in1) store_all_images(pf - off, pd, x + 1, y, z, Store<S>::st(o.y));
+        }
+        pf += pd.plane;
+      };
+      if (a.mode == 2) {
+#pragma unroll
+        for (int i = 0; i < QM; ++i) {
+          if (i >= Q) break;
+          put2(*reinterpret_cast<const float2*>(sg + (size_t)i * L::TILE));
+        }
+        return;
+      }
+      float2 A = f2(0.f), jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        const float2 ft = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(scr) + (size_t)i * L::TILE + n);
+        A = add2(A, ft);
+        jx = fma2(f2(vt.xi[i][0]), ft, jx);
+        jy = fma2(f2(vt.xi[i][1]), ft, jy);
+        if (D == 3) jz = fma2(f2(vt.xi[i][2]), ft, jz);
+      }
+      float2 sig[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) sig[i] = i < Q ? *reinterpret_cast<const float2*>(sg + (size_t)i * L::TILE) : f2(0.f);
+      const float2 rho = add2(f2(sc.rho_ref), A);
+      const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
+      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
+      float2 ca = f2(0.f), bx = f2(0.f), by = f2(0.f), bz = f2(0.f), bq = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        float2 s = mul2(f2(vt.xih[i][0]), uhx);
+        s = fma2(f2(vt.xih[i][1]), uhy, s);
+        if (D == 3) s = fma2(f2(vt.xih[i][2]), uhz, s);
+        // Phi, dPhi/ds, dPhi/dq of order N (isothermal)
+        const float2 s2 = mul2(s, s);
+        const float2 h = sub2(s2, q);
+        float2 ph = fma2(f2(0.5f), h, s), ps = add2(f2(1.f), s), pq = f2(-0.5f);
+        if (N >= 3) {
+          ph = fma2(f2(1.0f / 6.0f), mul2(s, sub2(s2, mul2(f2(3.f), q))), ph);
+          ps = fma2(f2(0.5f), h, ps);
+          pq = fma2(f2(-0.5f), s, pq);
+        }
+        const float2 v = mul2(f2(vt.w[i]), sig[i]);
+        // 1 + Phi - s dPhi/ds - 2 q dPhi/dq
+        const float2 term = fma2(mul2(f2(-2.f), q), pq, fma2(mul2(f2(-1.f), s), ps, add2(f2(1.f), ph)));
+        ca = fma2(v, term, ca);
+        const float2 vs = mul2(v, ps);
+        bx = fma2(vs, f2(vt.xih[i][0]), bx);
+        by = fma2(vs, f2(vt.xih[i][1]), by);
+        if (D == 3) bz = fma2(vs, f2(vt.xih[i][2]), bz);
+        bq = fma2(mul2(f2(2.f), v), pq, bq);
+      }
+      bx = fma2(bq, uhx, bx);
+      by = fma2(bq, uhy, by);
+      bz = fma2(bq, uhz, bz);
+      const float2 keep_s = f2(1.f - sc.inv_tau), itau = f2(sc.inv_tau);
+#pragma unroll
+      for (int k = 0; k < QM; ++k) {
+        if (k >= Q) break;
+        float2 g = fma2(bx, f2(vt.xih[k][0]), ca);
+        g = fma2(by, f2(vt.xih[k][1]), g);
+        if (D == 3) g = fma2(bz, f2(vt.xih[k][2]), g);
+        put2(fma2(keep_s, sig[k], mul2(g, itau)));
+      }
+    };
+
     // adjoint of the collision of one node (isothermal): staged planes
     // q < Q hold the pulled forward populations f~, planes Q + i the pulled
     // adjoint sigma_i.  mu_k = (1 - 1/tau) sigma_k + (a + b . xi^_k) / tau with
@@ -937,7 +1037,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
     };
 
-    if constexpr (ADJ) {
+    if constexpr (ADJ && APAIRS) {
+      for (int n = 2 * tid; n < L::TILE; n += 2 * NT) adjoint2(n);
+    } else if constexpr (ADJ) {
       for (int n = tid; n < L::TILE; n += NT) adjoint(n);
     } else if constexpr (PAIRS) {
       // the logging steps take the one-node path (its sums fit in registers)
