@@ -37,15 +37,22 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS (million node updates per second of the semi-Lagrangian LB step)"
 WORKLOAD = dict(velocity_set="D3Q27", n=128, Re=1600.0, Ma=0.1, courant=0.4, N=2, p=4, storage="fp32",
                 log_every=10)
+# other single-GPU workloads of the paper's configurations, for profiling (256^3 runs fit as well)
+WORKLOADS = {
+    "d3q27": WORKLOAD,
+    "d3q45": dict(WORKLOAD, velocity_set="D3Q45"),
+    "d3q45-comp": dict(WORKLOAD, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0),
+}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
 # default workload, from one ncu capture of the kernel source with this hash
 # (summary in profiles/); reported as null once the kernel source changes.
-TRAFFIC = {"kernel_sha": "99110e13180d72cf", "bytes": 315065600 + 308365824}
+TRAFFIC = {"kernel_sha": "663aaca45433b15b", "bytes": 292124928 + 292971520}
 
 
 def workload_name(w):
-    return (f"3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
+    kind = "compressible (f+g, gamma 1.4) " if w.get("compressible") else ""
+    return (f"{kind}3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
             f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
             f"{w['storage'].upper()} {'shifted ' if w['storage'] != 'fp64' else ''}storage, "
             f"k and dissipation every {w.get('log_every', 1)} steps")
@@ -334,7 +341,11 @@ def calibrate(prm, f, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
+    if w.get("compressible"):
+        print(json.dumps({"impl": "reference", "unavailable": "the timed oracle sample covers the isothermal "
+                          "workloads only"}), flush=True)
+        return
     prm, f = oracle_setup(w)
     budget = 150.0 / max(1, args.steps + args.warmup)
     npts = min(200000, calibrate(prm, f, budget))
@@ -363,6 +374,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-per-set", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="d3q27", choices=sorted(WORKLOADS),
+                    help="timed workload (the reported metric is quoted on the default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -382,7 +395,7 @@ def main():
     args.warmup = max(3, args.warmup)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
     sim, nodes = make_sim(w, torch)
     for _ in range(args.warmup):
         sim.step(1)
@@ -406,7 +419,7 @@ def main():
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_launch / t / 1e9
     sha = kernel_sha()
-    traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_sha"] == sha else None
+    traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_sha"] == sha and args.workload == "d3q27" else None
     sim.close()
     del sim
     if rank != 0:
@@ -420,7 +433,7 @@ def main():
     adjoint = [] if args.no_per_set else adjoint_table(torch)
     diagnostics = None if args.no_per_set else diagnostics_timing(torch)
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and not w.get("compressible"):
         prm, f = oracle_setup(w)
         npts = min(200000, calibrate(prm, f, 12.0))
         tc = oracle_time(prm, f, npts, 7)
