@@ -291,14 +291,17 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   // phase B on node pairs with the paired FP32 pipe (isothermal, FP32 arithmetic, up to 27 velocities)
   constexpr bool PAIRS = !ADJ && !COMP && std::is_same<C, float>::value && QM <= 27;
   constexpr bool APAIRS = ADJ && std::is_same<C, float>::value && QM <= 27 && N <= 3;
-  // phase B of the compressible FP32 sets reads its values from shared memory:
-  // chunks of NT nodes copied from the staging slab into the (then idle) boxes,
-  // double-buffered when two chunks fit (measured: +13% compressible D3Q45;
-  // the isothermal 45-velocity set is faster on the register path)
+  // phase B of the compressible FP32 sets and of the isothermal sets of more
+  // than 27 velocities reads its values from shared memory: chunks copied from
+  // the staging slab into the (then idle) boxes, double-buffered when two fit
   constexpr int SPMAX = COMP ? 2 * QM : QM;  // planes of a chunk
-  constexpr size_t SCHB = (size_t)SPMAX * L::NT * sizeof(C);
-  constexpr bool SMB = L::INPL && !ADJ && std::is_same<C, float>::value && COMP &&
-                       SCHB <= (size_t)L::NWG * L::WGB && L::TILE % L::NT == 0;
+  // isothermal sets of more than 27 velocities: node pairs on the paired FP32
+  // pipe, possible because the values come from shared memory, not registers
+  constexpr bool SPAIR = !COMP && QM > 27;
+  constexpr int CHN = SPAIR ? 2 * L::NT : L::NT;  // nodes of a chunk
+  constexpr size_t SCHB = (size_t)SPMAX * CHN * sizeof(C);
+  constexpr bool SMB = L::INPL && !ADJ && std::is_same<C, float>::value && (COMP || SPAIR) &&
+                       SCHB <= (size_t)L::NWG * L::WGB && L::TILE % CHN == 0;
   constexpr int SNBUF = 2 * SCHB <= (size_t)L::NWG * L::WGB ? 2 : 1;
   using T2 = typename PR::T;
   constexpr int NT = L::NT;
@@ -1053,6 +1056,78 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         pf += pd.plane;
       }
     };
+    // collide2 reading each node pair's values where they are used from a
+    // shared-memory chunk (src: the pair in plane 0, stride CH values)
+    auto collide2_from = [&](int n, const float* __restrict__ src, auto CHc) {
+      constexpr int CH = decltype(CHc)::value;
+      auto fv = [&](int i) { return *reinterpret_cast<const float2*>(src + i * CH); };
+      const int lx = n % L::TX, ly = (n / L::TX) % L::TY, lz = n / (L::TX * L::TY);
+      const int x = tx * L::TX + lx, y = ty * L::TY + ly, z = tz * L::TZ + lz;
+      if (x >= pd.n[0] || y >= pd.n[1] || z >= pd.n[2]) return;
+      const bool in1 = x + 1 < pd.n[0];
+      float2 A = f2(0.f), jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        const float2 fi = fv(i);
+        A = add2(A, fi);
+        jx = fma2(f2(vt.xi[i][0]), fi, jx);
+        jy = fma2(f2(vt.xi[i][1]), fi, jy);
+        if (D == 3) jz = fma2(f2(vt.xi[i][2]), fi, jz);
+      }
+      const float2 rho = add2(f2(sc.rho_ref), A);
+      const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
+      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
+      const float2 r2 = mul2(f2(0.5f), rho);
+      float2 c = fma2(f2(-1.f), mul2(r2, q), A);
+      float2 c1 = rho, c2 = r2, c3 = f2(0.f), c4 = f2(0.f);
+      if (N >= 3) {
+        c1 = fma2(f2(-1.f), mul2(r2, q), rho);
+        c3 = mul2(f2(1.0f / 6.0f), rho);
+      }
+      if (N >= 4) {
+        c = fma2(mul2(f2(0.125f), rho), mul2(q, q), c);
+        c2 = fma2(f2(-0.5f), mul2(r2, q), r2);
+        c4 = mul2(f2(1.0f / 24.0f), rho);
+      }
+      const float2 om = f2(1.f - sc.inv_tau);
+      const Images im = images_of(x, y, z);
+      const long long off = pad_index(pd, x, y, z);
+      S* pf = dst + off;
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= Q) break;
+        float2 s = mul2(f2(vt.xih[i][0]), uhx);
+        s = fma2(f2(vt.xih[i][1]), uhy, s);
+        if (D == 3) s = fma2(f2(vt.xih[i][2]), uhz, s);
+        float2 t = c2;
+        if (N >= 4) t = fma2(fma2(c4, s, c3), s, c2);
+        else if (N >= 3) t = fma2(c3, s, c2);
+        const float2 e = fma2(fma2(t, s, c1), s, c);  // A + rho Phi
+        const float2 o = fma2(om, fv(i), mul2(f2(vt.wt[i]), e));
+        if (simple) {
+          store_pair(pf, o.x, o.y);
+          if (im.n) {
+            store_pair(pf + im.i0, o.x, o.y);
+            if (im.n > 1) {
+              store_pair(pf + im.i1, o.x, o.y);
+              store_pair(pf + im.i2, o.x, o.y);
+              if (im.n > 3) {
+                store_pair(pf + im.i3, o.x, o.y);
+                store_pair(pf + im.i4, o.x, o.y);
+                store_pair(pf + im.i5, o.x, o.y);
+                store_pair(pf + im.i6, o.x, o.y);
+              }
+            }
+          }
+        } else {
+          store_all_images(pf - off, pd, x, y, z, Store<S>::st(o.x));
+          if (in1) store_all_images(pf - off, pd, x + 1, y, z, Store<S>::st(o.y));
+        }
+        pf += pd.plane;
+      }
+    };
 
     // The adjoint of the collision for two neighbouring nodes per thread on
     // the paired FP32 pipe (FP32, up to 27 velocities); same arithmetic as
@@ -1224,16 +1299,16 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     };
 
     if constexpr (SMB) {
-      constexpr int NCH = L::TILE / L::NT;
+      constexpr int NCH = L::TILE / CHN;
       C* sbuf = reinterpret_cast<C*>(base);
       auto stage = [&](int c, int b) {
         if (tid == 0) {
           // the chunk buffer was last read through the generic proxy
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          mbar_expect_tx(sbar + b, (unsigned)(planes * L::NT * sizeof(C)));
-          C* d = sbuf + (size_t)b * SPMAX * L::NT;
+          mbar_expect_tx(sbar + b, (unsigned)(planes * CHN * sizeof(C)));
+          C* d = sbuf + (size_t)b * SPMAX * CHN;
           for (int p = 0; p < planes; ++p)
-            bulk_g2s(d + p * L::NT, scr + (size_t)p * L::TILE + c * L::NT, (unsigned)(L::NT * sizeof(C)), sbar + b);
+            bulk_g2s(d + p * CHN, scr + (size_t)p * L::TILE + c * CHN, (unsigned)(CHN * sizeof(C)), sbar + b);
         }
         spend |= 1u << b;
       };
@@ -1247,11 +1322,20 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         }
         spar ^= 1u << b;
         spend &= ~(1u << b);
-        const C* src = sbuf + (size_t)b * SPMAX * L::NT + tid;
-        if (red)
-          collide_from(c * L::NT + tid, src, std::integral_constant<int, L::NT>(), std::true_type());
-        else
-          collide_from(c * L::NT + tid, src, std::integral_constant<int, L::NT>(), std::false_type());
+        const C* chunk = sbuf + (size_t)b * SPMAX * CHN;
+        if constexpr (SPAIR) {
+          if (red) {  // logging steps: one node at a time (the sums fit in registers)
+            for (int e = tid; e < CHN; e += L::NT)
+              collide_from(c * CHN + e, chunk + e, std::integral_constant<int, CHN>(), std::true_type());
+          } else {
+            collide2_from(c * CHN + 2 * tid, reinterpret_cast<const float*>(chunk) + 2 * tid,
+                          std::integral_constant<int, CHN>());
+          }
+        } else if (red) {
+          collide_from(c * CHN + tid, chunk + tid, std::integral_constant<int, CHN>(), std::true_type());
+        } else {
+          collide_from(c * CHN + tid, chunk + tid, std::integral_constant<int, CHN>(), std::false_type());
+        }
         __syncthreads();  // chunk buffer b read by every thread
         if (c + SNBUF < NCH) stage(c + SNBUF, b);
       }
