@@ -30,8 +30,17 @@
 
 #include "olb_step.cuh"
 
+// Unroll factor of the velocity loops of the shared-memory staged collision
+// (their values are read from shared memory, so the loops need not be fully
+// unrolled; a rolled loop keeps the code within the instruction cache).
+#ifndef OLB_STAGED_UNROLL
+#define OLB_STAGED_UNROLL 3
+#endif
+
 namespace olb {
 namespace wg {
+
+constexpr int STAGED_UNROLL = OLB_STAGED_UNROLL;
 
 constexpr int WGT = 128;  // threads per warpgroup
 
@@ -691,7 +700,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         hi = t;
       };
       C A = C(0), jx = C(0), jy = C(0), jz = C(0), Bp = C(0), Bh = C(0), Bl = C(0);
-#pragma unroll
+#pragma unroll STAGED_UNROLL
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
         const C fi = src[i * stride];
@@ -716,7 +725,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         merge(Bh, Bl, Bp);
         // sum of the pulled g (Sec. 3 temperature relation), FP32 groups merged exactly
         C Gp = C(0), Gh = C(0), Gl = C(0);
-#pragma unroll
+#pragma unroll STAGED_UNROLL
         for (int i = 0; i < QM; ++i) {
           if (i >= Q) break;
           Gp += src[(Q + i) * stride];
@@ -782,7 +791,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       // equilibrium (Appendix A), BGK (Sec. 3) and the stores: f first
       S* pf = dst + off;
       C Pi[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
-#pragma unroll
+#pragma unroll STAGED_UNROLL
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
         const C ph = phi(i);
@@ -798,7 +807,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       if (COMP) {
         // then g, the polynomial evaluated again
-#pragma unroll
+#pragma unroll STAGED_UNROLL
         for (int i = 0; i < QM; ++i) {
           if (i >= Q) break;
           const C geqd = vt.w[i] * sc.gfac * fma(rth, phi(i), gA);
