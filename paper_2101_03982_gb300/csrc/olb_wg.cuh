@@ -177,23 +177,6 @@ __device__ __forceinline__ void xrow(const C* s, const C* W, C out[4]) {
   }
 }
 
-template <int P, int VEC, int XO = 0, typename C>
-__device__ __forceinline__ void xrow_any(bool xact, int xo, const C* s, const C* W, C out[4]) {
-  if constexpr (XO == 0) {
-    if (!xact) {
-      xrow<P, 0, false>(s, W, out);
-      return;
-    }
-  }
-  if constexpr (XO < VEC) {
-    if (xo == XO) {
-      xrow<P, XO, true>(s, W, out);
-      return;
-    }
-    xrow_any<P, VEC, XO + 1>(true, xo, s, W, out);
-  }
-}
-
 __device__ __forceinline__ void wg_barrier(int wg) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(1 + wg), "r"(WGT) : "memory");
 }
