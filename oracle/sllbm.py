@@ -18,7 +18,11 @@ and notation, with no blocking or fusion:
 * equilibrium: Sec. 3 Hermite series, with the literal Hermite tensors and the
   literal equilibrium moments of Appendix A, contracted in full.
 * collision: Sec. 3 BGK; compressible relaxation time tau = mu/(c_s^2 dt P)+1/2
-  with P = rho theta T0 and g^eq = theta (2 C_v - D) f^eq.
+  with P = rho theta T0 and g^eq = theta (2 C_v - D) f^eq.  The dynamic
+  viscosity is constant in the paper; the optional power law
+  mu(theta) = mu theta^omega (omega = mu_exponent, 0 by default) is a
+  builder's extension, pinned by the decay of a shear wave at two
+  temperatures (the model's kinematic viscosity is mu(theta)/rho).
 
 Readings where the paper is silent (each listed in the design notes):
 T0 = c_s^2 of the set; C_v = 1/(gamma - 1); one step = pull, then collide, and
@@ -236,9 +240,10 @@ def temperature(vs, f, g, rho, u, gamma):
 class Params:
     """Run parameters of one simulation (grid units: dx, dt; tau or mu)."""
 
-    def __init__(self, vs, N, p, dt, dx, tau=None, compressible=False, gamma=1.4, mu=None):
+    def __init__(self, vs, N, p, dt, dx, tau=None, compressible=False, gamma=1.4, mu=None, mu_exponent=0.0):
         self.vs, self.N, self.p, self.dt, self.dx = vs, N, p, dt, dx
         self.tau, self.compressible, self.gamma, self.mu = tau, compressible, gamma, mu
+        self.mu_exponent = mu_exponent
         if compressible and mu is None:
             raise ValueError("compressible runs need the dynamic viscosity mu")
         if not compressible and tau is None:
@@ -262,7 +267,8 @@ def collide(prm, ft, gt=None):
     if prm.compressible:
         theta = temperature(vs, ft, gt, rho, u, prm.gamma)
         P = rho * theta * vs.cs ** 2
-        tau = prm.mu / (vs.cs ** 2 * prm.dt * P) + 0.5
+        mu = prm.mu * theta ** prm.mu_exponent  # power law in temperature; constant for omega = 0
+        tau = mu / (vs.cs ** 2 * prm.dt * P) + 0.5
     else:
         theta = np.ones_like(rho)
         tau = np.full_like(rho, prm.tau)
