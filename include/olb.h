@@ -90,6 +90,7 @@ typedef struct {
   int compressible;  /* 0: theta = 1, f only; 1: f and g, per-node tau(P) (requires c_s = 1) */
   double gamma;      /* heat capacity ratio (compressible), C_v = 1/(gamma-1) */
   double mu;         /* dynamic viscosity (compressible; the tau argument is then ignored) */
+  double mu_exponent; /* compressible: mu(theta) = mu theta^mu_exponent (0: constant mu, as in Sec. 3) */
   double rho0;       /* reference density of the shifted storage (default 1) */
   int allow_inexact; /* 1: accept a quadrature degree below 2N */
   int log_every;     /* the global sums are accumulated on steps whose count is a multiple of this (>= 1) */
@@ -100,7 +101,7 @@ typedef struct {
 typedef struct olb_ctx* olb_handle;
 
 /* Fill *opt with defaults: p = 3, FP64, cs_scale = 1, isothermal, gamma = 1.4,
- * mu = 0, rho0 = 1, allow_inexact = 0, log_every = 1, kernel = 0, stream = NULL. */
+ * mu = 0, mu_exponent = 0, rho0 = 1, allow_inexact = 0, log_every = 1, kernel = 0, stream = NULL. */
 void olb_default_options(olb_options* opt);
 
 /* Abscissae count Q, dimension D, c_s, largest |xi_{i,alpha}| and degree of a
@@ -174,7 +175,12 @@ int olb_set_populations(olb_handle h, const double* f, int on_device);
 
 /* Raw stored state (checkpoint): exactly olb_state_bytes() bytes, the
  * storage values (shifted where the storage is) as [planes][nz][ny][nx]
- * without ghost layers.  olb_set_state also refreshes the ghost layers. */
+ * without ghost layers.  olb_set_state also refreshes the ghost layers.
+ * With on_device = 0, a buffer in page-locked host memory that is mapped into
+ * the device's address space (cudaHostAlloc, cudaHostRegister, torch's
+ * pin_memory) is read or written in place by the copy kernel over the
+ * CPU-GPU link; other host memory goes through a temporary device buffer.
+ * Both return once the host buffer is no longer used. */
 size_t olb_state_bytes(olb_handle h);
 int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device);
 int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);

@@ -130,49 +130,80 @@ __global__ void __launch_bounds__(AUX_NT) moments_kernel(const __grid_constant__
   }
 }
 
-// compact element e = plane * nnodes + node
-template <typename S>
-__global__ void to_f64_kernel(const __grid_constant__ AuxArgs a, const S* state, double* f) {
-  const long long total = (long long)a.planes * a.nnodes;
-  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
-    const int p = (int)(e / a.nnodes);
-    int x, y, z;
-    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
-    f[e] = to_double(state[(long long)p * a.pad.plane + pad_index(a.pad, x, y, z)]) + a.base[p];
+// Row-wise walk over the compact layout [plane][z][y][x]: one warp per
+// (plane, z, y) row with its lanes along x, so that the compact and the padded
+// accesses are both coalesced and the row's coordinates are divided out once
+// per row instead of once per element.
+template <typename F>
+__device__ __forceinline__ void for_each_row(const AuxArgs& a, F&& f) {
+  const long long rows = (long long)a.planes * a.pad.n[2] * a.pad.n[1];
+  const long long nw = (long long)gridDim.x * (AUX_NT / 32);
+  for (long long r = blockIdx.x * (long long)(AUX_NT / 32) + (threadIdx.x >> 5); r < rows; r += nw) {
+    const long long pz = r / a.pad.n[1];
+    f(r, (int)(pz / a.pad.n[2]), (int)(r % a.pad.n[1]), (int)(pz % a.pad.n[2]), (int)(threadIdx.x & 31));
+  }
+}
+
+// Write one row of values (v(x) for x = lane, lane + 32, ...) at its nodes and
+// at every periodic copy in the ghost layers.  Four loads per lane are issued
+// before their stores, so that a source across the CPU-GPU link has enough
+// requests in flight.
+template <typename S, typename V>
+__device__ __forceinline__ void store_row_images(S* plane, const Padded& P, int y, int z, int lane, V&& v) {
+  const int fz = first_image(z, P.n[2], P.gl[2]), fy = first_image(y, P.n[1], P.gl[1]);
+  for (int x0 = lane; x0 < P.n[0]; x0 += 128) {
+    S val[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (x0 + 32 * k < P.n[0]) val[k] = v(x0 + 32 * k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = x0 + 32 * k;
+      if (x >= P.n[0]) break;
+      const int fx = first_image(x, P.n[0], P.gl[0]);
+      for (int cz = fz; cz < P.n[2] + P.gr[2]; cz += P.n[2])
+        for (int cy = fy; cy < P.n[1] + P.gr[1]; cy += P.n[1]) {
+          S* row = plane + pad_index(P, 0, cy, cz);
+          for (int cx = fx; cx < P.n[0] + P.gr[0]; cx += P.n[0]) row[cx] = val[k];
+        }
+    }
   }
 }
 
 template <typename S>
-__global__ void from_f64_kernel(const __grid_constant__ AuxArgs a, S* state, const double* f) {
-  const long long total = (long long)a.planes * a.nnodes;
-  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
-    const int p = (int)(e / a.nnodes);
-    int x, y, z;
-    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
-    store_all_images(state + (long long)p * a.pad.plane, a.pad, x, y, z, from_double<S>(f[e] - a.base[p]));
-  }
+__global__ void __launch_bounds__(AUX_NT) to_f64_kernel(const __grid_constant__ AuxArgs a, const S* state, double* f) {
+  for_each_row(a, [&](long long r, int p, int y, int z, int lane) {
+    const S* src = state + (long long)p * a.pad.plane + pad_index(a.pad, 0, y, z);
+    const double b = a.base[p];
+    for (int x = lane; x < a.pad.n[0]; x += 32) f[r * a.pad.n[0] + x] = to_double(src[x]) + b;
+  });
 }
 
 template <typename S>
-__global__ void gather_kernel(const __grid_constant__ AuxArgs a, const S* state, S* compact) {
-  const long long total = (long long)a.planes * a.nnodes;
-  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
-    const int p = (int)(e / a.nnodes);
-    int x, y, z;
-    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
-    compact[e] = state[(long long)p * a.pad.plane + pad_index(a.pad, x, y, z)];
-  }
+__global__ void __launch_bounds__(AUX_NT) from_f64_kernel(const __grid_constant__ AuxArgs a, S* state, const double* f) {
+  for_each_row(a, [&](long long r, int p, int y, int z, int lane) {
+    const double* src = f + r * a.pad.n[0];
+    const double b = a.base[p];
+    store_row_images(state + (long long)p * a.pad.plane, a.pad, y, z, lane,
+                     [&](int x) { return from_double<S>(src[x] - b); });
+  });
 }
 
 template <typename S>
-__global__ void scatter_kernel(const __grid_constant__ AuxArgs a, S* state, const S* compact) {
-  const long long total = (long long)a.planes * a.nnodes;
-  for (long long e = blockIdx.x * (long long)AUX_NT + threadIdx.x; e < total; e += (long long)gridDim.x * AUX_NT) {
-    const int p = (int)(e / a.nnodes);
-    int x, y, z;
-    node_xyz(a.pad, e - (long long)p * a.nnodes, x, y, z);
-    store_all_images(state + (long long)p * a.pad.plane, a.pad, x, y, z, compact[e]);
-  }
+__global__ void __launch_bounds__(AUX_NT) gather_kernel(const __grid_constant__ AuxArgs a, const S* state, S* compact) {
+  for_each_row(a, [&](long long r, int p, int y, int z, int lane) {
+    const S* src = state + (long long)p * a.pad.plane + pad_index(a.pad, 0, y, z);
+    S* dst = compact + r * a.pad.n[0];
+    for (int x = lane; x < a.pad.n[0]; x += 32) dst[x] = src[x];
+  });
+}
+
+template <typename S>
+__global__ void __launch_bounds__(AUX_NT) scatter_kernel(const __grid_constant__ AuxArgs a, S* state, const S* compact) {
+  for_each_row(a, [&](long long r, int p, int y, int z, int lane) {
+    const S* src = compact + r * a.pad.n[0];
+    store_row_images(state + (long long)p * a.pad.plane, a.pad, y, z, lane, [&](int x) { return src[x]; });
+  });
 }
 
 // Seed of the adjoint sweep: lam_i = dJ/df_i for J(rho, u) given dJ/drho and
@@ -323,6 +354,9 @@ int aux_grid(long long work) {
   return (int)g;
 }
 
+// One warp per (plane, z, y) row.
+int row_grid(const AuxArgs& a) { return aux_grid((long long)a.planes * a.pad.n[2] * a.pad.n[1] * 32); }
+
 template <typename F>
 int by_storage(int storage, F&& f) {
   switch (storage) {
@@ -357,7 +391,7 @@ int launch_state_moments(const AuxArgs& a, const void* state, double* rho, doubl
 int launch_to_f64(const AuxArgs& a, const void* state, double* f, void* stream) {
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    to_f64_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state, f);
+    to_f64_kernel<S><<<row_grid(a), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state, f);
     return (int)cudaGetLastError();
   });
 }
@@ -365,7 +399,7 @@ int launch_to_f64(const AuxArgs& a, const void* state, double* f, void* stream) 
 int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream) {
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    from_f64_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, f);
+    from_f64_kernel<S><<<row_grid(a), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, f);
     return (int)cudaGetLastError();
   });
 }
@@ -373,7 +407,7 @@ int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream
 int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream) {
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    gather_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state,
+    gather_kernel<S><<<row_grid(a), AUX_NT, 0, (cudaStream_t)stream>>>(a, (const S*)state,
                                                                                                     (S*)compact);
     return (int)cudaGetLastError();
   });
@@ -382,7 +416,7 @@ int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stre
 int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream) {
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    scatter_kernel<S><<<aux_grid((long long)a.planes * a.nnodes), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state,
+    scatter_kernel<S><<<row_grid(a), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state,
                                                                                                      (const S*)compact);
     return (int)cudaGetLastError();
   });

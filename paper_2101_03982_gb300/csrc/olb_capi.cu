@@ -39,7 +39,7 @@ void olb::set_last_error(const std::string& msg) { g_last_error = msg; }
 struct olb_ctx {
   olb_grid grid{};
   int vs_id = 0, N = 2, p = 3, storage = 0, comp = 0, allow_inexact = 0;
-  double tau = 1.0, dt = 0.0, gamma = 1.4, mu = 0.0, rho0 = 1.0, cs = 1.0, cs_scale = 1.0;
+  double tau = 1.0, dt = 0.0, gamma = 1.4, mu = 0.0, mu_exp = 0.0, rho0 = 1.0, cs = 1.0, cs_scale = 1.0;
   VelocitySet set{};  // scaled abscissae
   int Q = 0, planes = 0, D = 0, elem = 8;
   long long nnodes = 0;
@@ -379,6 +379,20 @@ int copy_out(olb_ctx* h, void* dst, const void* dev_src, size_t bytes, int on_de
   return on_device ? OLB_OK : stream_sync(h, 0);
 }
 
+// Device address of host memory that the GPU can read and write in place:
+// page-locked memory mapped into the device's address space (cudaHostAlloc or
+// cudaHostRegister under unified addressing).  Kernels then move the bytes over
+// the CPU-GPU link themselves, with no staging copy.  Null for any other
+// memory (pageable host memory goes through a device buffer and a copy).
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Device staging buffer for host-side FP64 arrays (freed by the caller).
 int dev_alloc(olb_ctx* h, void** p, size_t bytes) {
   cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
@@ -566,6 +580,7 @@ void olb_default_options(olb_options* opt) {
   opt->compressible = 0;
   opt->gamma = 1.4;
   opt->mu = 0.0;
+  opt->mu_exponent = 0.0;
   opt->rho0 = 1.0;
   opt->allow_inexact = 0;
   opt->log_every = 1;
@@ -629,6 +644,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
       return fail(OLB_EUNSUPPORTED, "compressible runs need c_s = 1 (T0 = 1)");
     if (!(opt.gamma > 1.0)) return fail(OLB_EINVAL, "gamma must exceed 1");
     if (!(opt.mu > 0.0)) return fail(OLB_EINVAL, "compressible runs need mu > 0");
+    if (!std::isfinite(opt.mu_exponent)) return fail(OLB_EINVAL, "mu_exponent must be finite");
   } else if (!(tau > 0.5) || !std::isfinite(tau)) {
     return fail(OLB_EINVAL, "tau must exceed 1/2");
   }
@@ -650,6 +666,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->dt = dt;
   h->gamma = opt.gamma;
   h->mu = opt.mu;
+  h->mu_exp = opt.compressible ? opt.mu_exponent : 0.0;
   h->rho0 = opt.rho0;
   h->cs_scale = opt.cs_scale;
   h->cs = cs;
@@ -712,6 +729,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   a.tau = tau;
   a.inv_tau = 1.0 / tau;
   a.mu_dt = h->mu / (cs * cs * dt);
+  a.mu_exp = h->mu_exp;
   a.two_cv = 2.0 * Cv;
   a.gfac = 2.0 * Cv - h->D;
   a.inv_cs = 1.0 / cs;
@@ -726,6 +744,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   a.f_inv_cs = (float)a.inv_cs;
   a.f_cs2 = (float)a.cs2;
   a.f_dt = (float)a.dt;
+  a.f_mu_exp = (float)a.mu_exp;
 
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -1039,13 +1058,17 @@ int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device) {
   if (rc) return rc;
   void* d = buf;
   void* tmp = nullptr;
-  if (!on_device) {
+  void* mapped = on_device ? nullptr : mapped_host(buf);
+  if (mapped) {
+    d = mapped;  // the gather writes the host buffer directly
+  } else if (!on_device) {
     rc = dev_alloc(h, &tmp, bytes);
     if (rc) return rc;
     d = tmp;
   }
   rc = launch_rc(launch_gather(h->aux, h->buf[h->cur], d, h->stream), "gather");
-  if (rc == OLB_OK && !on_device) rc = copy_out(h, buf, d, bytes, 0);
+  if (rc == OLB_OK && mapped) rc = stream_sync(h, 0);
+  if (rc == OLB_OK && tmp) rc = copy_out(h, buf, d, bytes, 0);
   if (tmp) {
     cudaFreeAsync(tmp, h->stream);
     int r2 = stream_sync(h, 0);
@@ -1061,7 +1084,10 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
   if (rc) return rc;
   const void* d = buf;
   void* tmp = nullptr;
-  if (!on_device) {
+  const void* mapped = on_device ? nullptr : mapped_host(buf);
+  if (mapped) {
+    d = mapped;  // the scatter reads the host buffer directly
+  } else if (!on_device) {
     rc = dev_alloc(h, &tmp, bytes);
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(tmp, buf, bytes, cudaMemcpyHostToDevice, h->stream);
@@ -1069,6 +1095,7 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
     d = tmp;
   }
   if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], d, h->stream), "scatter");
+  if (rc == OLB_OK && mapped) rc = stream_sync(h, 0);
   if (tmp) {
     cudaFreeAsync(tmp, h->stream);
     int r2 = stream_sync(h, 0);

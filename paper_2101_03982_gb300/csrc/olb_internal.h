@@ -101,6 +101,7 @@ struct StepArgs {
   double inv_tau;       // isothermal 1/tau
   double tau;           // isothermal tau
   double mu_dt;         // compressible: mu / (c_s^2 dt)
+  double mu_exp;        // compressible: mu(theta) = mu theta^mu_exp
   double two_cv;        // 2 C_v
   double gfac;          // 2 C_v - D
   double inv_cs;        // 1 / c_s
@@ -108,7 +109,7 @@ struct StepArgs {
   double dt;
   // the same scalars rounded to FP32 for the FP32-arithmetic kernels (no
   // double-to-float conversions on the device)
-  float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt;
+  float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt, f_mu_exp;
 };
 
 // Launch of the fused step for storage `storage` (olb_storage); returns a

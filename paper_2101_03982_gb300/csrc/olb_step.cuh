@@ -420,6 +420,17 @@ __device__ __forceinline__ void xpass_any(bool xact, int xo, const SRC* src, int
   xpass_dispatch_rec<D, P, S, SRC, 0>(xo, src, qx, ly, lz, W, out);
 }
 
+// mu(theta) / (c_s^2 dt) of the power law mu theta^omega; omega = 0, the
+// constant viscosity of Sec. 3, skips the power.
+__device__ __forceinline__ float mu_theta(float mu_dt, float theta, float omega) {
+  if (omega == 0.f) return mu_dt;
+  return mu_dt * powf(theta, omega);
+}
+__device__ __forceinline__ double mu_theta(double mu_dt, double theta, double omega) {
+  if (omega == 0.0) return mu_dt;
+  return mu_dt * pow(theta, omega);
+}
+
 // ---------------------------------------------------------------------------
 // periodic copies of a node in the ghost layers
 // ---------------------------------------------------------------------------
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(NT, 1)
         const double X = Bd[e] + Gd[e] - jj / r - a.two_cv * (double)Ad[e];
         const C thm1 = C(X) / (C(a.two_cv) * rho[e]);
         const C theta = C(1) + thm1;
-        const C tau = C(a.mu_dt) / (rho[e] * theta) + C(0.5);
+        const C tau = mu_theta(C(a.mu_dt), theta, C(a.mu_exp)) / (rho[e] * theta) + C(0.5);
         itau[e] = C(1) / tau;
         tt[e] = thm1;
         gA[e] = fma(rho[e], thm1, Ad[e]);

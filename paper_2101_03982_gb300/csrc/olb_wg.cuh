@@ -81,17 +81,17 @@ template <typename C>
 struct Scal;
 template <>
 struct Scal<float> {
-  float rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt;
+  float rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp;
   __device__ __forceinline__ explicit Scal(const StepArgs& a)
       : rho_ref(a.f_rho_ref), inv_tau(a.f_inv_tau), tau(a.f_tau), mu_dt(a.f_mu_dt), two_cv(a.f_two_cv),
-        gfac(a.f_gfac), inv_cs(a.f_inv_cs), cs2(a.f_cs2), dt(a.f_dt) {}
+        gfac(a.f_gfac), inv_cs(a.f_inv_cs), cs2(a.f_cs2), dt(a.f_dt), mu_exp(a.f_mu_exp) {}
 };
 template <>
 struct Scal<double> {
-  double rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt;
+  double rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp;
   __device__ __forceinline__ explicit Scal(const StepArgs& a)
       : rho_ref(a.rho_ref), inv_tau(a.inv_tau), tau(a.tau), mu_dt(a.mu_dt), two_cv(a.two_cv), gfac(a.gfac),
-        inv_cs(a.inv_cs), cs2(a.cs2), dt(a.dt) {}
+        inv_cs(a.inv_cs), cs2(a.cs2), dt(a.dt), mu_exp(a.mu_exp) {}
 };
 
 // Two values of the arithmetic type; FP32 pairs use the paired FMA.
@@ -723,7 +723,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const double X = fma(-a.two_cv, (double)A, (((double)Bh + (double)Bl) + ((double)Gh + (double)Gl)) - (double)K);
         tt = C(X) / (sc.two_cv * rho);
         theta = C(1) + tt;
-        tau = sc.mu_dt / (rho * theta) + C(0.5);
+        tau = mu_theta(sc.mu_dt, theta, sc.mu_exp) / (rho * theta) + C(0.5);
         itau = C(1) / tau;
         gA = fma(rho, tt, A);
         rth = rho * theta;
@@ -874,7 +874,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const double X = fma(-a.two_cv, (double)A, (((double)Bh + (double)Bl) + ((double)Gh + (double)Gl)) - (double)K);
         tt = C(X) / (sc.two_cv * rho);
         theta = C(1) + tt;
-        tau = sc.mu_dt / (rho * theta) + C(0.5);
+        tau = mu_theta(sc.mu_dt, theta, sc.mu_exp) / (rho * theta) + C(0.5);
         itau = C(1) / tau;
         gA = fma(rho, tt, A);
         rth = rho * theta;

@@ -65,6 +65,15 @@ def _create(olb, dim=3, n=(16, 16, 16), vs="D3Q27", N=2, tau=0.8, dt=0.01, **kw)
     return rc, h
 
 
+def test_default_options_layout(olb):
+    """The binding's struct and the library agree field by field."""
+    o = olb.Options()
+    olb.lib().olb_default_options(ctypes.byref(o))
+    assert (o.interp_order, o.storage, o.cs_scale, o.compressible) == (3, 0, 1.0, 0)
+    assert (o.gamma, o.mu, o.mu_exponent, o.rho0) == (1.4, 0.0, 0.0, 1.0)
+    assert (o.allow_inexact, o.log_every, o.kernel, o.stream) == (0, 1, 0, None)
+
+
 @pytest.mark.parametrize("kw,code", [
     (dict(dim=4), -1),
     (dict(n=(0, 4, 4)), -1),
@@ -77,6 +86,7 @@ def _create(olb, dim=3, n=(16, 16, 16), vs="D3Q27", N=2, tau=0.8, dt=0.01, **kw)
     (dict(vs="D2Q9"), -1),                      # set dimension differs from the grid's
     (dict(N=3), -7),                            # D3Q27 has degree 5 < 2N = 6
     (dict(vs="D3Q21", compressible=1, mu=0.1), -7),  # c_s = sqrt(3/5) != 1
+    (dict(vs="D3Q45", N=4, compressible=1, mu=0.1, mu_exponent=float("nan")), -1),
 ])
 def test_argument_checks(olb, kw, code):
     rc, h = _create(olb, **kw)

@@ -31,15 +31,15 @@ def olb():
 
 
 def make_pair(olb, name, shape, N=2, p=4, storage="fp64", comp=False, courant=0.4, cs_scale=1.0, tau=0.7,
-              mu=0.02, gamma=1.4, seed=1, kernel="auto"):
+              mu=0.02, gamma=1.4, seed=1, kernel="auto", mu_exponent=0.0):
     vs = V.get(name)
     if cs_scale != 1.0:
         vs = vs.scaled(cs_scale)
     dx = 0.05
     dt = courant * dx / np.abs(vs.xi).max()
-    prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=tau, compressible=comp, gamma=gamma, mu=mu)
+    prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=tau, compressible=comp, gamma=gamma, mu=mu, mu_exponent=mu_exponent)
     sim = olb.Sim(shape, dx, name, N, tau, dt, interp_order=p, storage=storage, cs_scale=cs_scale,
-                  compressible=comp, gamma=gamma, mu=mu, kernel=kernel)
+                  compressible=comp, gamma=gamma, mu=mu, kernel=kernel, mu_exponent=mu_exponent)
     rng = np.random.default_rng(seed)
     grid = tuple(reversed(shape))
     rho = 1.0 + 0.05 * rng.uniform(-1, 1, grid)
@@ -128,9 +128,26 @@ def test_one_step_parity_generic_kernel(olb, name, shape, N, p, storage, comp, c
     _one_step(olb, name, shape, N, p, storage, comp, courant, cs, "generic")
 
 
-def _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel):
+MU_OF_THETA = [
+    ("D2Q19", (40, 70), 4, "fp64", "auto", 0.7),
+    ("D3Q45", (34, 10, 9), 3, "fp64", "auto", -0.5),
+    ("D3Q45", (32, 16, 10), 4, "fp32", "auto", 0.7),
+    ("D2Q19", (40, 70), 4, "fp32", "auto", 0.7),
+    ("D3Q45", (16, 12, 10), 4, "fp32", "generic", 0.7),
+    ("D3Q45", (16, 12, 10), 4, "fp64", "generic", 0.7),
+]
+
+
+@pytest.mark.parametrize("name,shape,p,storage,kernel,omega", MU_OF_THETA)
+def test_one_step_parity_viscosity_power_law(olb, name, shape, p, storage, kernel, omega):
+    """Compressible step with mu(theta) = mu theta^omega in every kernel that
+    runs the compressible collision."""
+    _one_step(olb, name, shape, 4, p, storage, True, 0.4, 1.0, kernel, mu_exponent=omega)
+
+
+def _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel, mu_exponent=0.0):
     sim, prm, state = make_pair(olb, name, shape, N=N, p=p, storage=storage, comp=comp, courant=courant,
-                                cs_scale=cs, kernel=kernel)
+                                cs_scale=cs, kernel=kernel, mu_exponent=mu_exponent)
     want, diag = oracle_steps(prm, state)
     sim.step(1)
     got = sim.get_populations(np.zeros_like(state))
@@ -231,6 +248,45 @@ def test_state_round_trip_and_device_pointers(olb):
     f = torch.zeros(state.shape, dtype=torch.float64, device="cuda")
     sim.get_populations(f)
     assert np.allclose(f.cpu().numpy(), state, rtol=0, atol=0)
+    sim.close()
+
+
+@pytest.mark.parametrize("name,shape,p,storage", [("D3Q27", (37, 11, 9), 4, "fp32"), ("D3Q27", (33, 9, 10), 3, "fp64"),
+                                                   ("D3Q27", (40, 20, 18), 4, "fp16")])
+def test_set_state_fills_the_ghost_copies(olb, name, shape, p, storage):
+    """A state written back through the compact copy steps exactly as the
+    original: every periodic copy in the ghost layers was refilled (ragged
+    rows included)."""
+    sim, prm, state = make_pair(olb, name, shape, N=2, p=p, storage=storage)
+    raw = torch.empty(sim.state_bytes(), dtype=torch.uint8, device="cuda")
+    sim.get_state(raw)
+    sim.step(2)
+    want = sim.get_populations(np.zeros_like(state))
+    sim.step(1)
+    sim.set_state(raw.cpu().numpy())
+    sim.step(2)
+    got = sim.get_populations(np.zeros_like(state))
+    assert np.array_equal(got, want)
+    sim.close()
+
+
+def test_state_through_pinned_host_memory(olb):
+    """Page-locked host buffers are read and written in place by the copy
+    kernels: the same bytes as through device memory, and a state set from
+    one steps exactly as the original."""
+    sim, prm, state = make_pair(olb, "D3Q27", (37, 11, 9), N=2, p=4, storage="fp32")
+    nb = sim.state_bytes()
+    dev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    pinned = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    sim.get_state(dev)
+    sim.get_state(pinned)
+    assert torch.equal(pinned, dev.cpu())
+    sim.step(2)
+    want = sim.get_populations(np.zeros_like(state))
+    sim.step(1)
+    sim.set_state(pinned)
+    sim.step(2)
+    assert np.array_equal(sim.get_populations(np.zeros_like(state)), want)
     sim.close()
 
 
