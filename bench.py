@@ -334,8 +334,12 @@ def oracle_time(prm, f, npts, seed):
 
 
 def calibrate(prm, f, seconds):
-    t = oracle_time(prm, f, 512, 0)
-    return max(256, int(512 * seconds / max(t, 1e-6)))
+    """Sample size whose oracle step takes about `seconds`: a fixed cost plus a
+    per-node cost, fitted from two small timings."""
+    t1 = oracle_time(prm, f, 512, 0)
+    t2 = oracle_time(prm, f, 4096, 1)
+    per_node = max((t2 - t1) / (4096 - 512), 1e-9)
+    return max(256, int((seconds - max(t1 - 512 * per_node, 0.0)) / per_node))
 
 
 def slowest_rank_time(t, dist, torch, device):
