@@ -42,6 +42,7 @@ WORKLOADS = {
     "d3q27": WORKLOAD,
     "d3q45": dict(WORKLOAD, velocity_set="D3Q45"),
     "d3q45-comp": dict(WORKLOAD, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0),
+    "d3q27-fp64": dict(WORKLOAD, storage="fp64"),
 }
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
@@ -56,6 +57,26 @@ def workload_name(w):
             f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
             f"{w['storage'].upper()} {'shifted ' if w['storage'] != 'fp64' else ''}storage, "
             f"k and dissipation every {w.get('log_every', 1)} steps")
+
+
+def algorithmic_flops(w):
+    """Arithmetic of one node update in the step's own formulation (an FMA
+    counts two): the separable pull, 2 (p + 1) per active axis of every
+    velocity (f, and g when compressible); the moments, 1 + 2D per velocity
+    (+ 3 with g: |xi|^2 f and g); 2 + 4D per node (rho, 1/rho, u, u/c_s, q;
+    + 10 for the temperature); per velocity the equilibrium (s = xi^.u^: 2D,
+    Horner polynomial of degree N in s: 2N, weight and density: 2; + 8 for the
+    temperature-dependent coefficients) and BGK (3; + 4 for g)."""
+    from paper_2101_03982_gb300 import olb
+    xi, _ = olb.velocity_set_table(w["velocity_set"])
+    Q, D = xi.shape
+    comp = bool(w.get("compressible"))
+    nnz = int((np.abs(xi) > 0).sum())
+    pull = 2 * (w["p"] + 1) * nnz * (2 if comp else 1)
+    moments = Q * (1 + 2 * D + (3 if comp else 0))
+    node = 2 + 4 * D + (10 if comp else 0)
+    per_vel = Q * (2 * D + 2 * w["N"] + 2 + 3 + (12 if comp else 0))
+    return pull + moments + node + per_vel
 
 
 def kernel_sha():
@@ -197,6 +218,8 @@ def per_set_table(torch, flush):
                       Ma=1.2, Re=800.0, courant=0.4))
     specs.append(dict(velocity_set="D2Q9", n=64, N=2, p=3, storage="fp64", courant=0.4, Re=100.0, Ma=0.0866))
     hbm, _ = measured_peaks()
+    from paper_2101_03982_gb300 import olb
+    fp64_peak = olb.fp64_fma_peak(torch.cuda.current_stream().cuda_stream) / 1e12
     for w in specs:
         try:
             sim, nodes = make_sim(w, torch)
@@ -212,6 +235,10 @@ def per_set_table(torch, flush):
                          N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
                          mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
                          gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))
+        if w["storage"] == "fp64":  # bound by the FP64 pipe: % of the measured FP64 FMA peak first
+            fl = algorithmic_flops(w) * nodes / t / 1e12
+            rows[-1].update(fp64_tflops=round(fl, 4), fp64_peak_tflops=round(fp64_peak, 4),
+                            fp64_alu_frac=round(fl / fp64_peak, 4), flops_per_node=algorithmic_flops(w))
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -433,6 +460,9 @@ def main():
     bytes_per_launch = 2 * sim.planes * s * nodes
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_launch / t / 1e9
+    if w["storage"] == "fp64":  # the FP64 pipe bounds the FP64 step: measure its FMA peak on this GPU
+        fp64_peak = olb.fp64_fma_peak(torch.cuda.current_stream().cuda_stream) / 1e12
+        flops_per_launch = algorithmic_flops(w) * nodes
     sha = kernel_sha()
     traffic = TRAFFIC["bytes"] if TRAFFIC["kernel_sha"] == sha and args.workload == "d3q27" else None
     sim.close()
@@ -450,7 +480,7 @@ def main():
     cpu = None
     if not args.no_cpu and not w.get("compressible"):
         prm, f = oracle_setup(w)
-        npts = min(200000, calibrate(prm, f, 12.0))
+        npts = min(400000, calibrate(prm, f, 16.0))
         tc = oracle_time(prm, f, npts, 7)
         cpu = {"value": npts / tc / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"{npts} random nodes of the {w['n']}^3 workload, one step (oracle step_at_points, "
@@ -466,7 +496,13 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "kernel": "sl_wg_kernel (two-phase fused pull + collide)"},
+                     "kernel": "sl_wg_kernel (two-phase fused pull + collide)"} if w["storage"] != "fp64" else
+                    {"bound": "alu", "achieved": flops_per_launch / t / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": flops_per_launch / t / 1e12 / fp64_peak, "traffic": None,
+                     "peak_source": "measured: FP64 FMA loop (olb_fp64_fma_peak) on this GPU",
+                     "algorithmic_flops_per_launch": flops_per_launch,
+                     "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
+                     "kernel": "sl_wg_kernel (two-phase fused pull + collide), FP64"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,

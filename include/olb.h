@@ -247,6 +247,15 @@ int olb_equilibrium_vjp(olb_handle h, const double* rho, const double* u, const 
 int olb_state_sums_noalloc(int velocity_set, const olb_grid* grid, int storage, double cs_scale,
                            double rho0, const void* populations, double* out, void* stream);
 
+/* Measured FP64 FMA throughput of the current device, in flop/s (an FMA is two
+ * flops): the denominator of the FP64 step's roofline, which the narrow FP64
+ * pipe bounds rather than HBM (Sec. 3's step in FP64 storage).  Runs a fixed
+ * FMA loop (8 independent chains per thread, 4 blocks of 256 threads per SM)
+ * on `stream` (cudaStream_t or NULL), synchronises it, and returns the best of
+ * three timed launches after a warm-up (about 0.2 s in all).  OLB_ECUDA if a
+ * launch or an event fails. */
+int olb_fp64_fma_peak(void* stream, double* flops_per_s);
+
 /* Message for an error code, and the calling thread's most recent failure. */
 const char* olb_strerror(int code);
 const char* olb_last_error(void);

@@ -75,6 +75,7 @@ def lib():
             "olb_adjoint_step": (i, [vp, vp, vp, i]),
             "olb_moments_vjp": (i, [vp, vp, vp, vp, i]),
             "olb_equilibrium_vjp": (i, [vp, vp, vp, vp, vp, vp, i]),
+            "olb_fp64_fma_peak": (i, [vp, dp]),
             "olb_strerror": (ctypes.c_char_p, [i]),
             "olb_last_error": (ctypes.c_char_p, []),
         }
@@ -99,6 +100,13 @@ def velocity_set_info(name):
     _check(lib().olb_velocity_set_info(VELOCITY_SETS[name], ctypes.byref(Q), ctypes.byref(D), ctypes.byref(cs),
                                        ctypes.byref(mx), ctypes.byref(deg)))
     return Q.value, D.value, cs.value, mx.value, deg.value
+
+
+def fp64_fma_peak(stream=None):
+    """Measured FP64 FMA throughput of the current device in flop/s."""
+    out = ctypes.c_double()
+    _check(lib().olb_fp64_fma_peak(stream, ctypes.byref(out)))
+    return out.value
 
 
 def velocity_set_table(name):
