@@ -6,6 +6,7 @@ and the CPU-baseline leg of ``bench.py`` may import it; the product path (the
 CUDA library and its binding) never does, and the oracle imports nothing from
 the product.
 
-Parity unpinned: ``sllbm.strain_dissipation`` (a builder's estimator with no
-formula in the paper) is checked only for agreement with the CUDA path.
+``sllbm.strain_dissipation`` is a builder's estimator (no formula in the
+paper); it is pinned by the analytic strain of the 3D Taylor-Green vortex
+(tests/test_oracle_step.py).
 """

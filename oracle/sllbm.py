@@ -30,8 +30,8 @@ the stored state is post-collision; f at t = 0 is the equilibrium of the
 initial fields.
 
 Parity pins: see tests/test_oracle_*.py.  The dissipation estimator
-``strain_dissipation`` is a builder's quantity (no formula in the paper):
-parity unpinned beyond its agreement with the CUDA path.
+``strain_dissipation`` is a builder's quantity (no formula in the paper),
+pinned by the analytic strain of the decaying 3D Taylor-Green vortex.
 """
 import itertools
 import math
@@ -366,7 +366,8 @@ def strain_dissipation(prm, diag):
     """Builder's estimator: eps = mean 2 nu S:S with S = -Pi_neq / (2 P tau dt).
 
     Pi_neq = sum_i xi_i xi_i (f~_i - f_i^eq) (Chapman-Enskog); P = rho theta c_s^2;
-    nu = c_s^2 theta dt (tau - 1/2).  Parity unpinned against the paper.
+    nu = c_s^2 theta dt (tau - 1/2).  Not in the paper; pinned by the analytic
+    strain of the 3D Taylor-Green vortex, 2 nu <S:S> = (3/4) nu u0^2 e^(-6 nu t).
     """
     vs = prm.vs
     fneq = diag["ft"] - diag["feq"]
