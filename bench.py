@@ -43,6 +43,8 @@ WORKLOADS = {
     "d3q45": dict(WORKLOAD, velocity_set="D3Q45"),
     "d3q45-comp": dict(WORKLOAD, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0),
     "d3q27-fp64": dict(WORKLOAD, storage="fp64"),
+    "d2q19-comp": dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
+                       Ma=1.2, Re=800.0, courant=0.4),
 }
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
@@ -52,6 +54,10 @@ TRAFFIC = {"kernel_sha": "cb7d144d64dae53c", "bytes": 293803520 + 294396672}
 
 
 def workload_name(w):
+    if "shape" in w:  # the 2D shock-vortex field
+        return (f"2D shock-vortex interaction (Mach {w['Ma']:g} shock, isentropic vortex), {w['shape'][0]}x"
+                f"{w['shape'][1]} periodic, {w['velocity_set']}, N={w['N']} Hermite equilibrium, f+g, gamma 1.4, "
+                f"p={w['p']} Lagrange pull, Courant {w['courant']}, {w['storage'].upper()} shifted storage")
     kind = "compressible (f+g, gamma 1.4) " if w.get("compressible") else ""
     return (f"{kind}3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
             f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
