@@ -44,6 +44,8 @@ constexpr int STAGED_UNROLL = OLB_STAGED_UNROLL;
 
 constexpr int WGT = 128;  // threads per warpgroup
 
+constexpr size_t roundup_sz(size_t a, size_t m) { return (a + m - 1) / m * m; }
+
 template <int D, int P, typename S>
 struct GLayout {
   using C = typename Store<S>::C;
@@ -74,6 +76,33 @@ struct GLayout {
   // two mbarriers per warpgroup (its boxes) and two for the shared-memory staging of phase B
   static constexpr size_t BYTES = OFF_M + (2 * NWG + 2) * sizeof(unsigned long long) + 128;
   static_assert(NWG >= 1, "one warpgroup must fit");
+};
+
+// Shared-memory staging of phase B.  The compressible FP32 sets and the
+// isothermal sets of more than 27 velocities read their pulled values from
+// shared memory instead of registers: after phase A the staging slab is
+// copied, one chunk of CHN nodes at a time, into shared memory.  3D in-place
+// kernels use their (then idle) boxes, double-buffered when two chunks fit;
+// the 2D compressible kernels keep issuing box copies through phase B and
+// get one dedicated chunk buffer after the rest of their shared memory.
+template <int D, int P, typename S, bool COMP, int QM, bool ADJ>
+struct Staging {
+  using L = GLayout<D, P, S>;
+  using C = typename Store<S>::C;
+  static constexpr int SPMAX = COMP ? 2 * QM : QM;  // planes of a chunk
+  // isothermal sets of more than 27 velocities: node pairs on the paired FP32
+  // pipe, possible because the values come from shared memory, not registers
+  static constexpr bool SPAIR = !COMP && QM > 27;
+  static constexpr int CHN = SPAIR ? 2 * L::NT : L::NT;  // nodes of a chunk
+  static constexpr size_t SCHB = (size_t)SPMAX * CHN * sizeof(C);
+  static constexpr bool FP32 = !ADJ && std::is_same<C, float>::value && L::TILE % CHN == 0;
+  static constexpr bool IN_BOXES = FP32 && L::INPL && (COMP || SPAIR) && SCHB <= (size_t)L::NWG * L::WGB;
+  static constexpr size_t OFF_S = roundup_sz(L::OFF_M + (2 * L::NWG + 2) * sizeof(unsigned long long), 128);
+  static constexpr bool OWN = FP32 && D == 2 && COMP && OFF_S + SCHB + 128 <= L::BUDGET;
+  static constexpr bool SMB = IN_BOXES || OWN;
+  static constexpr int SNBUF = (IN_BOXES && 2 * SCHB <= (size_t)L::NWG * L::WGB) ? 2 : 1;
+  // dynamic shared memory of the launch
+  static constexpr size_t BYTES = OWN ? OFF_S + SCHB + 128 : L::BYTES;
 };
 
 // Scalars of the step in the arithmetic type.
@@ -283,18 +312,13 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   // phase B on node pairs with the paired FP32 pipe (isothermal, FP32 arithmetic, up to 27 velocities)
   constexpr bool PAIRS = !ADJ && !COMP && std::is_same<C, float>::value && QM <= 27;
   constexpr bool APAIRS = ADJ && std::is_same<C, float>::value && QM <= 27 && N <= 3;
-  // phase B of the compressible FP32 sets and of the isothermal sets of more
-  // than 27 velocities reads its values from shared memory: chunks copied from
-  // the staging slab into the (then idle) boxes, double-buffered when two fit
-  constexpr int SPMAX = COMP ? 2 * QM : QM;  // planes of a chunk
-  // isothermal sets of more than 27 velocities: node pairs on the paired FP32
-  // pipe, possible because the values come from shared memory, not registers
-  constexpr bool SPAIR = !COMP && QM > 27;
-  constexpr int CHN = SPAIR ? 2 * L::NT : L::NT;  // nodes of a chunk
-  constexpr size_t SCHB = (size_t)SPMAX * CHN * sizeof(C);
-  constexpr bool SMB = L::INPL && !ADJ && std::is_same<C, float>::value && (COMP || SPAIR) &&
-                       SCHB <= (size_t)L::NWG * L::WGB && L::TILE % CHN == 0;
-  constexpr int SNBUF = 2 * SCHB <= (size_t)L::NWG * L::WGB ? 2 : 1;
+  // phase B from shared-memory chunks of the staging slab (see Staging)
+  using SG = Staging<D, P, S, COMP, QM, ADJ>;
+  constexpr int SPMAX = SG::SPMAX;
+  constexpr bool SPAIR = SG::SPAIR;
+  constexpr int CHN = SG::CHN;
+  constexpr bool SMB = SG::SMB;
+  constexpr int SNBUF = SG::SNBUF;
   using T2 = typename PR::T;
   constexpr int NT = L::NT;
   extern __shared__ unsigned char smem_raw[];
@@ -1292,7 +1316,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
     if constexpr (SMB) {
       constexpr int NCH = L::TILE / CHN;
-      C* sbuf = reinterpret_cast<C*>(base);
+      C* sbuf = reinterpret_cast<C*>(base + (SG::OWN ? SG::OFF_S : 0));
       auto stage = [&](int c, int b) {
         if (tid == 0) {
           // the chunk buffer was last read through the generic proxy
@@ -1332,9 +1356,10 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         if (c + SNBUF < NCH) stage(c + SNBUF, b);
       }
       if (failed) break;
-      // the boxes are free again: the next tile's first two copies of each warpgroup
+      // the boxes are free again: the next tile's first two copies of each
+      // warpgroup (the one-box pull of the 2D kernels has issued its own)
       const int tn = tile + gridDim.x;
-      if (tn < a.ntiles && nplan > 0) {
+      if (SG::IN_BOXES && tn < a.ntiles && nplan > 0) {
         if (wt == 0) issue(tn, sched.plane[wg][0], cb);
         if (cb) pending1 = true;
         else pending = true;
@@ -1443,22 +1468,24 @@ template <int D, int P, typename S, bool COMP, int QM, int N>
 int launch_wg(const StepLaunch& Lc) {
   using C = typename Store<S>::C;
   using Lay = GLayout<D, P, S>;
+  constexpr size_t bytes = Staging<D, P, S, COMP, QM, false>::BYTES;
   auto kern = sl_wg_kernel<D, P, S, COMP, QM, N>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     attr_done = true;
   }
   const auto& vt = *static_cast<const VelTab<C>*>(Lc.veltab);
   const auto& st = *static_cast<const StencilTab<C, P + 1>*>(Lc.stentab);
-  kern<<<Lc.grid, Lay::NT, Lay::BYTES, static_cast<cudaStream_t>(Lc.stream)>>>(Lc.a, vt, st, *Lc.maps, *Lc.sched);
+  kern<<<Lc.grid, Lay::NT, bytes, static_cast<cudaStream_t>(Lc.stream)>>>(Lc.a, vt, st, *Lc.maps, *Lc.sched);
   return (int)cudaGetLastError();
 }
 
 template <int D, int P, typename S, bool COMP, int QM, int N>
 int occupancy_wg(StepInfo* o) {
   using Lay = GLayout<D, P, S>;
+  constexpr size_t bytes = Staging<D, P, S, COMP, QM, false>::BYTES;
   auto kern = sl_wg_kernel<D, P, S, COMP, QM, N>;
   o->bxw = Lay::BXW;
   o->by = Lay::BY;
@@ -1468,12 +1495,11 @@ int occupancy_wg(StepInfo* o) {
   o->ty = Lay::TY;
   o->tz = Lay::TZ;
   o->vec = Lay::VEC;
-  o->smem = Lay::BYTES;
+  o->smem = bytes;
   o->wg = Lay::NWG;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::BYTES) != cudaSuccess)
-    return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Lay::NT, Lay::BYTES) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Lay::NT, bytes) != cudaSuccess) return 0;
   return n;
 }
 
