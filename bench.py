@@ -50,7 +50,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
 # default workload, from one ncu capture of the kernel source with this hash
 # (summary in profiles/); reported as null once the kernel source changes.
-TRAFFIC = {"kernel_sha": "cb7d144d64dae53c", "bytes": 293803520 + 294396672}
+TRAFFIC = {"kernel_sha": "dd89cab1bda0b3f8", "bytes": 292900352 + 293401088}
 
 
 def workload_name(w):
