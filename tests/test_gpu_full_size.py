@@ -11,7 +11,8 @@ stored values it needs from the device state node by node, in FP64.
 
 Cases: the 3D Taylor-Green vortex (Re 1600, Ma 0.1, p = 4, Courant 0.4) with
 D3Q27 in FP32 and FP64 at 128^3 and D3Q45 (N = 2) in FP32 at 256^3, and the
-compressible Taylor-Green vortex (D3Q45, N = 4, f + g, Ma 1.0) in FP32 at 256^3.
+compressible Taylor-Green vortex (D3Q45, N = 4, f + g, Ma 1.0) in FP32 at 256^3
+and at 512^3, the largest workload (99 GB of A/B buffers).
 Bounds as in the small-grid parity tests: FP32 2e-5 of the largest stored
 deviation, FP64 1e-12 of the largest population.
 """
@@ -60,6 +61,14 @@ def stored_planes(sim, dtype):
     return raw.view(dtype)
 
 
+def base_of(prm, storage, comp):
+    Q = prm.vs.Q
+    if storage == "fp64":
+        return np.zeros(2 * Q if comp else Q)
+    w = prm.vs.w
+    return np.concatenate([w, w * (2.0 / (prm.gamma - 1.0) - 3)]) if comp else w
+
+
 def make_case(olb, name, n, storage, comp):
     from paper_2101_03982_gb300 import inputs, params
     if comp:
@@ -87,11 +96,7 @@ def test_sampled_nodes_at_full_size(olb, name, n, storage, comp):
     sim, prm = make_case(olb, name, n, storage, comp)
     Q = prm.vs.Q
     dtype = torch.float64 if storage == "fp64" else torch.float32
-    if storage == "fp64":
-        base = np.zeros(2 * Q if comp else Q)
-    else:
-        w = prm.vs.w
-        base = np.concatenate([w, w * (2.0 / (prm.gamma - 1.0) - 3)]) if comp else w
+    base = base_of(prm, storage, comp)
     before = stored_planes(sim, dtype).view(-1, n, n, n)
     sim.step(1)
     after = stored_planes(sim, dtype).view(-1, n, n, n)
@@ -109,3 +114,31 @@ def test_sampled_nodes_at_full_size(olb, name, n, storage, comp):
         err = np.abs(got - want).max() / np.abs(want - base[:, None]).max()
         assert err < 2e-5, err
     sim.close()
+
+
+def test_sampled_nodes_at_512_cubed(olb):
+    """The compressible D3Q45 workload at 512^3 (f + g, FP32): 99 GB of A/B
+    buffers and a 48 GB compact copy of the state, the largest configuration.
+    The oracle's values are taken from the copy before the step, which is then
+    released, so the device holds at most about 150 GB."""
+    import gc
+    gc.collect()
+    torch.cuda.empty_cache()
+    n, Q = 512, 45
+    sim, prm = make_case(olb, "D3Q45", n, "fp32", True)
+    base = base_of(prm, "fp32", True)
+    pts = np.random.default_rng(512).integers(0, n, (NPTS, 3))
+    before = stored_planes(sim, torch.float32).view(-1, n, n, n)
+    fpost, gpost, _ = O.step_at_points(prm, DevState(before[:Q], base[:Q]), DevState(before[Q:], base[Q:]), pts)
+    want = np.concatenate([fpost, gpost])
+    del before
+    torch.cuda.empty_cache()
+    sim.step(1)
+    after = stored_planes(sim, torch.float32).view(-1, n, n, n)
+    idx = tuple(torch.as_tensor(pts[:, a], device="cuda") for a in (2, 1, 0))
+    got = after[:, idx[0], idx[1], idx[2]].double().cpu().numpy() + base[:, None]
+    del after
+    sim.close()
+    torch.cuda.empty_cache()
+    err = np.abs(got - want).max() / np.abs(want - base[:, None]).max()
+    assert err < 2e-5, err
