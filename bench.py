@@ -218,6 +218,7 @@ def per_set_table(torch, flush):
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0))
+    specs.append(dict(WORKLOAD, n=512, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0))  # 99 GB of A/B
     specs.append(dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
                       Ma=1.2, Re=800.0, courant=0.4))
     specs.append(dict(velocity_set="D2Q25", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
