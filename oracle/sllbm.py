@@ -97,6 +97,46 @@ def pull_plane(plane, delta, p):
     return out
 
 
+def pull_plane_xbc(plane, delta, p, inflow):
+    """The pull of ``pull_plane`` with non-periodic x (the standing-shock set-up
+    of Sec. 4.1): departure points left of the domain (x < 0) read the inflow
+    value, a fixed post-collision equilibrium, and points right of it
+    (x >= nx) read the last column (zero-gradient outflow); y and z stay
+    periodic.  This boundary treatment is a reading: the paper states none.
+    """
+    D = plane.ndim
+    nx = plane.shape[-1]
+    sts = [stencil_1d(float(delta[a]), p) for a in range(D)]
+    pad = p + int(math.ceil(abs(float(delta[0])))) + 1
+    left = np.full(plane.shape[:-1] + (pad,), float(inflow))
+    right = np.repeat(plane[..., -1:], pad, axis=-1)
+    ext = np.concatenate([left, plane, right], axis=-1)
+    out = np.zeros_like(plane)
+    for js in itertools.product(range(p + 1), repeat=D):
+        weight = 1.0
+        shifts = []
+        for a in range(D):
+            m0, W = sts[a]
+            weight *= W[js[a]]
+            shifts.append(m0 + js[a])
+        moved = ext[..., pad + shifts[0]:pad + shifts[0] + nx]
+        for a in range(1, D):
+            moved = np.roll(moved, -shifts[a], axis=D - 1 - a)
+        out += weight * moved
+    return out
+
+
+def inflow_populations(prm, rho, u, theta=1.0):
+    """Equilibrium populations (f_in, g_in or None) of one inflow state."""
+    vs = prm.vs
+    feq = equilibrium(vs, np.array([float(rho)]), np.asarray(u, dtype=np.float64).reshape(1, vs.D),
+                      np.array([float(theta)]), prm.N)[:, 0]
+    if not prm.compressible:
+        return feq, None
+    Cv = 1.0 / (prm.gamma - 1.0)
+    return feq, float(theta) * (2.0 * Cv - vs.D) * feq
+
+
 def pull_point(plane, delta, p, point):
     """Interpolated value of one field at one node (brute-force loop form)."""
     D = plane.ndim
@@ -250,10 +290,16 @@ class Params:
             raise ValueError("isothermal runs need tau")
 
 
-def pull_state(prm, f):
-    """Apply the semi-Lagrangian pull to every population field. f: (Q, *grid)."""
+def pull_state(prm, f, inflow=None):
+    """Apply the semi-Lagrangian pull to every population field. f: (Q, *grid).
+
+    inflow: None (periodic), or the inflow value of every field (Q,) for the
+    non-periodic x of ``pull_plane_xbc``."""
     deltas = departure_offsets(prm.vs.xi, prm.dt, prm.dx)
-    return np.stack([pull_plane(f[i], deltas[i], prm.p) for i in range(f.shape[0])])
+    Q = prm.vs.Q
+    if inflow is None:
+        return np.stack([pull_plane(f[i], deltas[i], prm.p) for i in range(f.shape[0])])
+    return np.stack([pull_plane_xbc(f[i], deltas[i % Q], prm.p, inflow[i]) for i in range(f.shape[0])])
 
 
 def collide(prm, ft, gt=None):
@@ -283,15 +329,18 @@ def collide(prm, ft, gt=None):
     return fpost, gpost, diag
 
 
-def step(prm, f, g=None):
+def step(prm, f, g=None, xbc=None):
     """One SLLBM step: pull every population, then collide (BGK).
 
     f (Q, *grid) post-collision state at t; returns the post-collision state
-    at t + dt and per-step diagnostics.
+    at t + dt and per-step diagnostics.  xbc: None (periodic), or
+    ``inflow_populations`` of the inflow state for the non-periodic x of
+    ``pull_plane_xbc``.
     """
     grid = f.shape[1:]
-    ft = pull_state(prm, f).reshape(f.shape[0], -1)
-    gt = pull_state(prm, g).reshape(g.shape[0], -1) if prm.compressible else None
+    f_in, g_in = xbc if xbc is not None else (None, None)
+    ft = pull_state(prm, f, f_in).reshape(f.shape[0], -1)
+    gt = pull_state(prm, g, g_in).reshape(g.shape[0], -1) if prm.compressible else None
     fpost, gpost, diag = collide(prm, ft, gt)
     diag.update(reductions(prm, diag))
     fpost = fpost.reshape(f.shape)
