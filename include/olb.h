@@ -173,6 +173,19 @@ int olb_enstrophy(olb_handle h, double* enstrophy);
 int olb_get_populations(olb_handle h, double* f, int on_device);
 int olb_set_populations(olb_handle h, const double* f, int on_device);
 
+/* Non-periodic x for the standing shock of Sec. 4.1 (the paper does not state
+ * its boundary treatment; this is a reading).  kind 1: after every writer of
+ * the state (each step, init, set_populations, set_state) the ghost columns
+ * left of x = 0 are set to the equilibrium of the inflow state (rho, u[D],
+ * theta; theta is ignored for isothermal runs) and those right of x = nx - 1
+ * to copies of the last column (zero-gradient outflow); y and z stay
+ * periodic.  The current state's ghosts are refilled at once.  kind 0:
+ * periodic again (every ghost copy rewritten from the interior).  OLB_EINVAL
+ * for another kind, a null u, rho <= 0 or a non-finite value (theta <= 0 when
+ * compressible).  The adjoint and the tape (olb_tape_*, olb_adjoint_step)
+ * return OLB_EUNSUPPORTED while kind 1 is set. */
+int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, double theta);
+
 /* Raw stored state (checkpoint): exactly olb_state_bytes() bytes, the
  * storage values (shifted where the storage is) as [planes][nz][ny][nx]
  * without ghost layers.  olb_set_state also refreshes the ghost layers.

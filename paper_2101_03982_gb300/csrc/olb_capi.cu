@@ -54,6 +54,8 @@ struct olb_ctx {
   int force_generic = 0;
   long long step_count = 0;
   int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
+  int xbc = 0;             // 1: non-periodic x (inflow / zero-gradient outflow ghost columns)
+  XInflow inflow{};
   Padded pad{};
   TmaMaps maps{};
   WgSchedule sched{};
@@ -406,6 +408,12 @@ int launch_rc(int rc, const char* what) {
   return cuda_fail((cudaError_t)rc, what);
 }
 
+// Refill the x ghost columns of buffer b when x is not periodic.
+int apply_xbc(olb_ctx* h, void* b) {
+  if (!h->xbc) return OLB_OK;
+  return launch_rc(launch_xbc(h->aux, b, h->inflow, h->stream), "x boundary");
+}
+
 // Launch description of the forward step on the handle's buffers.
 StepLaunch base_launch(olb_ctx* h) {
   StepLaunch L{};
@@ -460,6 +468,7 @@ void fill_adj_tabs(olb_ctx* h) {
 
 // Buffers, tables and schedules of the adjoint sweep (once per handle).
 int adj_prepare(olb_ctx* h) {
+  if (h->xbc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for periodic grids only");
   if (h->adj_ready) return OLB_OK;
   if (h->comp) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the isothermal step only");
   if (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED)
@@ -870,6 +879,7 @@ int olb_init_fields(olb_handle h, const double* rho, const double* u, const doub
     dth = theta ? t + n * (1 + h->D) : nullptr;
   }
   rc = launch_rc(launch_init_fields(h->aux, h->buf[h->cur], dr, du, dth, h->stream), "init_fields");
+  if (rc == OLB_OK) rc = apply_xbc(h, h->buf[h->cur]);
   if (tmp) {
     cudaFreeAsync(tmp, h->stream);
     if (rc == OLB_OK) rc = stream_sync(h, 0);
@@ -892,6 +902,8 @@ int olb_step(olb_handle h, int n) {
     rc = launch_rc(r, "sl_step");
     if (rc) return rc;
     h->cur ^= 1;
+    rc = apply_xbc(h, h->buf[h->cur]);
+    if (rc) return rc;
     h->step_count = count;
     h->partials_valid = L.a.reduce;
   }
@@ -1035,6 +1047,7 @@ int olb_set_populations(olb_handle h, const double* f, int on_device) {
     d = static_cast<const double*>(tmp);
   }
   if (rc == OLB_OK) rc = launch_rc(launch_from_f64(h->aux, h->buf[h->cur], d, h->stream), "from_f64");
+  if (rc == OLB_OK) rc = apply_xbc(h, h->buf[h->cur]);
   if (tmp) {
     cudaFreeAsync(tmp, h->stream);
     int r2 = stream_sync(h, 0);
@@ -1095,6 +1108,7 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
     d = tmp;
   }
   if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], d, h->stream), "scatter");
+  if (rc == OLB_OK) rc = apply_xbc(h, h->buf[h->cur]);
   if (rc == OLB_OK && mapped) rc = stream_sync(h, 0);
   if (tmp) {
     cudaFreeAsync(tmp, h->stream);
@@ -1103,6 +1117,40 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
   }
   h->partials_valid = 0;
   return rc;
+}
+
+int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, double theta) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (kind != 0 && kind != 1) return fail(OLB_EINVAL, "x boundary kind must be 0 (periodic) or 1 (inflow/outflow)");
+  if (kind == 1) {
+    if (!u) return fail(OLB_EINVAL, "null inflow velocity");
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(OLB_EINVAL, "inflow density must be positive");
+    if (h->comp && (!(theta > 0.0) || !std::isfinite(theta)))
+      return fail(OLB_EINVAL, "inflow temperature must be positive");
+    for (int a = 0; a < h->D; ++a)
+      if (!std::isfinite(u[a])) return fail(OLB_EINVAL, "inflow velocity must be finite");
+  }
+  int rc = set_device(h);
+  if (rc) return rc;
+  if (kind == 1) {
+    h->inflow.rho = rho;
+    for (int a = 0; a < 3; ++a) h->inflow.u[a] = a < h->D ? u[a] : 0.0;
+    h->inflow.theta = h->comp ? theta : 1.0;
+    h->xbc = 1;
+    return apply_xbc(h, h->buf[h->cur]);
+  }
+  if (!h->xbc) return OLB_OK;
+  // back to periodic: rewrite every ghost copy from the interior
+  h->xbc = 0;
+  const size_t bytes = (size_t)h->planes * h->nnodes * h->elem;
+  void* tmp = nullptr;
+  rc = dev_alloc(h, &tmp, bytes);
+  if (rc) return rc;
+  rc = launch_rc(launch_gather(h->aux, h->buf[h->cur], tmp, h->stream), "gather");
+  if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], tmp, h->stream), "scatter");
+  cudaFreeAsync(tmp, h->stream);
+  int r2 = stream_sync(h, 0);
+  return rc == OLB_OK ? r2 : rc;
 }
 
 int olb_synchronize(olb_handle h, int timeout_ms) {
@@ -1126,6 +1174,7 @@ int olb_tape_reserve(olb_handle h, int nslots) {
 
 int olb_tape_record(olb_handle h, int n) {
   if (!h) return fail(OLB_EINVAL, "null handle");
+  if (h->xbc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for periodic grids only");
   if (n < 0) return fail(OLB_EINVAL, "negative step count");
   if (n + 1 > (int)h->tape.size()) return fail(OLB_EBOUNDS, "tape has fewer than n + 1 slots");
   int rc = set_device(h);

@@ -183,6 +183,13 @@ int launch_from_f64(const AuxArgs& a, void* state, const double* f, void* stream
 int launch_gather(const AuxArgs& a, const void* state, void* compact, void* stream);
 int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* stream);
 int launch_reduce_final(const double* partials, int nslots, double* out, void* stream);
+// Inflow state of the non-periodic x: rho, u (3 components, 0 beyond D), theta.
+struct XInflow {
+  double rho, u[3], theta;
+};
+// Refill the x ghost columns: inflow equilibrium on the left, copies of the
+// last column on the right (every plane, every padded row).
+int launch_xbc(const AuxArgs& a, void* state, const XInflow& in, void* stream);
 // Per-block partial sums of |curl u|^2 (slot 0 of NRED per block) of the
 // velocity u [D][n] (FP64), fourth-order central differences of spacing dx.
 int launch_enstrophy(const AuxArgs& a, const double* u, double dx, double* partials, int grid, void* stream);

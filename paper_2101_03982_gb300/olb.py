@@ -76,6 +76,7 @@ def lib():
             "olb_moments_vjp": (i, [vp, vp, vp, vp, i]),
             "olb_equilibrium_vjp": (i, [vp, vp, vp, vp, vp, vp, i]),
             "olb_fp64_fma_peak": (i, [vp, dp]),
+            "olb_set_x_boundary": (i, [vp, i, d, dp, d]),
             "olb_strerror": (ctypes.c_char_p, [i]),
             "olb_last_error": (ctypes.c_char_p, []),
         }
@@ -266,6 +267,13 @@ class Sim:
         W = np.zeros((self.Q, 3, self.interp_order + 1))
         _check(lib().olb_stencil(self._h, m0.ctypes.data, W.ctypes.data))
         return m0, W
+
+    def set_x_boundary(self, kind, rho=1.0, u=None, theta=1.0):
+        """kind "periodic", or "inflow_outflow" with the inflow state (rho, u (D,), theta)."""
+        k = {"periodic": 0, "inflow_outflow": 1}[kind]
+        uu = np.zeros(3) if u is None else np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+        _check(lib().olb_set_x_boundary(self._h, k, float(rho), uu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        float(theta)))
 
     def synchronize(self, timeout_ms=0):
         _check(lib().olb_synchronize(self._h, int(timeout_ms)))
