@@ -55,8 +55,9 @@ TRAFFIC = {"kernel_sha": "dd89cab1bda0b3f8", "bytes": 292900352 + 293401088}
 
 def workload_name(w):
     if "shape" in w:  # the 2D shock-vortex field
-        return (f"2D shock-vortex interaction (Mach {w['Ma']:g} shock, isentropic vortex), {w['shape'][0]}x"
-                f"{w['shape'][1]} periodic, {w['velocity_set']}, N={w['N']} Hermite equilibrium, f+g, gamma 1.4, "
+        return (f"2D shock-vortex interaction (Mach {w['Ma']:g} standing shock, isentropic vortex), {w['shape'][0]}x"
+                f"{w['shape'][1]}, inflow/outflow in x, periodic in y, {w['velocity_set']}, N={w['N']} Hermite "
+                f"equilibrium, f+g, gamma 1.4, "
                 f"p={w['p']} Lagrange pull, Courant {w['courant']}, {w['storage'].upper()} shifted storage")
     kind = "compressible (f+g, gamma 1.4) " if w.get("compressible") else ""
     return (f"{kind}3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
@@ -163,9 +164,11 @@ def make_sim(w, torch):
             sim = olb.Sim((nx, ny), 1.0, w["velocity_set"], w["N"], 1.0, dt, interp_order=w["p"],
                           storage=w["storage"], compressible=True, gamma=1.4, mu=mu,
                           log_every=w.get("log_every", 10))
-            rho, u, th = inputs.shock_vortex(nx, ny)
+            rho, u, th = inputs.shock_vortex(nx, ny, Ma_a=w["Ma"])
             sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda(),
                             torch.from_numpy(th).cuda())
+            # standing shock: the upstream state flows in at x = 0, zero-gradient outflow at x = nx - 1
+            sim.set_x_boundary("inflow_outflow", 1.0, (w["Ma"] * math.sqrt(1.4), 0.0), 1.0)
             return sim, int(nx * ny)
         rp = params.tgv_compressible(w["velocity_set"], w["n"], w["Re"], w["Ma"], w["courant"])
         sim = olb.Sim((w["n"],) * 3, rp.dx, w["velocity_set"], w["N"], rp.tau, rp.dt, interp_order=w["p"],
@@ -512,7 +515,7 @@ def main():
                      "kernel": "sl_wg_kernel (two-phase fused pull + collide), FP64"},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if "shape" in w else 1),  # the 2D shock adds its x-boundary fill
         "clocks": clk.summary(),
         "k_final": k,
         "per_set": per_set,

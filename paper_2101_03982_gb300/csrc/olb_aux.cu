@@ -209,29 +209,39 @@ __global__ void __launch_bounds__(AUX_NT) scatter_kernel(const __grid_constant__
 // Non-periodic x (inflow and outflow, the standing-shock set-up of Sec. 4.1):
 // the ghost columns left of x = 0 hold the equilibrium of the inflow state
 // (its post-collision populations), those right of x = nx - 1 repeat the last
-// column (zero-gradient outflow).  One warp per padded (plane, z, y) row,
-// ghost rows included, after every writer of the state.
+// column (zero-gradient outflow).
+//
+// The inflow value of every plane, in storage form, computed once when the
+// boundary is set (one thread per plane; FP64 as the initialisation).
 template <typename S>
-__global__ void __launch_bounds__(AUX_NT) xbc_kernel(const __grid_constant__ AuxArgs a, S* state, XInflow in) {
+__global__ void xbc_values_kernel(const __grid_constant__ AuxArgs a, XInflow in, S* vals) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.planes) return;
+  const bool comp = a.compressible != 0;
+  const double uhx = in.u[0] * a.inv_cs, uhy = in.u[1] * a.inv_cs, uhz = in.u[2] * a.inv_cs;
+  const double q = uhx * uhx + uhy * uhy + uhz * uhz;
+  const double r = in.rho, th = comp ? in.theta : 1.0, t = th - 1.0, A = r - a.rho_ref;
+  const int i = p < a.Q ? p : p - a.Q;
+  const double xr = a.xih[i][0] * a.xih[i][0] + a.xih[i][1] * a.xih[i][1] + a.xih[i][2] * a.xih[i][2];
+  const double rD = xr - a.D, rp = xr * xr - 2.0 * (a.D + 2) * xr + a.D * (a.D + 2.0);
+  const double s = a.xih[i][0] * uhx + a.xih[i][1] * uhy + a.xih[i][2] * uhz;
+  const double ph = comp ? phi_m1<double, true>(s, q, t, rD, rp, a.N) : phi_m1<double, false>(s, q, t, rD, rp, a.N);
+  vals[p] = from_double<S>(p < a.Q ? a.w[i] * (A + r * ph) : a.w[i] * a.gfac * (r * t + A + r * th * ph));
+}
+
+// The ghost fill, after every writer of the state: one warp per padded
+// (plane, z, y) row, ghost rows included.
+template <typename S>
+__global__ void __launch_bounds__(AUX_NT) xbc_kernel(const __grid_constant__ AuxArgs a, S* state, const S* vals) {
   const Padded& P = a.pad;
   const long long rows_pp = (long long)P.np[1] * P.np[2];
   const long long rows = (long long)a.planes * rows_pp;
   const long long nw = (long long)gridDim.x * (AUX_NT / 32);
   const int lane = threadIdx.x & 31;
-  const bool comp = a.compressible != 0;
-  const double uhx = in.u[0] * a.inv_cs, uhy = in.u[1] * a.inv_cs, uhz = in.u[2] * a.inv_cs;
-  const double q = uhx * uhx + uhy * uhy + uhz * uhz;
-  const double r = in.rho, th = comp ? in.theta : 1.0, t = th - 1.0, A = r - a.rho_ref;
   for (long long row = blockIdx.x * (long long)(AUX_NT / 32) + (threadIdx.x >> 5); row < rows; row += nw) {
     const int p = (int)(row / rows_pp);
     S* line = state + (long long)p * P.plane + (row - (long long)p * rows_pp) * P.np[0];
-    const int i = p < a.Q ? p : p - a.Q;
-    const double xr = a.xih[i][0] * a.xih[i][0] + a.xih[i][1] * a.xih[i][1] + a.xih[i][2] * a.xih[i][2];
-    const double rD = xr - a.D, rp = xr * xr - 2.0 * (a.D + 2) * xr + a.D * (a.D + 2.0);
-    const double s = a.xih[i][0] * uhx + a.xih[i][1] * uhy + a.xih[i][2] * uhz;
-    const double ph = comp ? phi_m1<double, true>(s, q, t, rD, rp, a.N) : phi_m1<double, false>(s, q, t, rD, rp, a.N);
-    const double v = p < a.Q ? a.w[i] * (A + r * ph) : a.w[i] * a.gfac * (r * t + A + r * th * ph);
-    const S vin = from_double<S>(v);
+    const S vin = vals[p];
     for (int k = lane; k < P.gl[0]; k += 32) line[k] = vin;
     const S last = line[P.gl[0] + P.n[0] - 1];
     for (int k = lane; k < P.gr[0]; k += 32) line[P.gl[0] + P.n[0] + k] = last;
@@ -454,11 +464,19 @@ int launch_scatter(const AuxArgs& a, void* state, const void* compact, void* str
   });
 }
 
-int launch_xbc(const AuxArgs& a, void* state, const XInflow& in, void* stream) {
+int launch_xbc_values(const AuxArgs& a, const XInflow& in, void* vals, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    xbc_values_kernel<S><<<(a.planes + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, in, (S*)vals);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_xbc(const AuxArgs& a, void* state, const void* vals, void* stream) {
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     const long long rows = (long long)a.planes * a.pad.np[1] * a.pad.np[2];
-    xbc_kernel<S><<<aux_grid(rows * 32), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, in);
+    xbc_kernel<S><<<aux_grid(rows * 32), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state, (const S*)vals);
     return (int)cudaGetLastError();
   });
 }

@@ -56,6 +56,7 @@ struct olb_ctx {
   int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
   int xbc = 0;             // 1: non-periodic x (inflow / zero-gradient outflow ghost columns)
   XInflow inflow{};
+  void* xbc_vals = nullptr;  // inflow value per plane, storage form
   Padded pad{};
   TmaMaps maps{};
   WgSchedule sched{};
@@ -205,6 +206,7 @@ void release(olb_ctx* h) {
     if (h->adj[k]) cudaFree(h->adj[k]);
   if (h->adj_scratch) cudaFree(h->adj_scratch);
   if (h->ens_u) cudaFree(h->ens_u);
+  if (h->xbc_vals) cudaFree(h->xbc_vals);
   if (h->ens_part) cudaFree(h->ens_part);
   delete h;
 }
@@ -411,7 +413,7 @@ int launch_rc(int rc, const char* what) {
 // Refill the x ghost columns of buffer b when x is not periodic.
 int apply_xbc(olb_ctx* h, void* b) {
   if (!h->xbc) return OLB_OK;
-  return launch_rc(launch_xbc(h->aux, b, h->inflow, h->stream), "x boundary");
+  return launch_rc(launch_xbc(h->aux, b, h->xbc_vals, h->stream), "x boundary");
 }
 
 // Launch description of the forward step on the handle's buffers.
@@ -1133,9 +1135,18 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
   int rc = set_device(h);
   if (rc) return rc;
   if (kind == 1) {
+    if (!h->xbc_vals) {
+      cudaError_t e = cudaMalloc(&h->xbc_vals, (size_t)h->planes * h->elem);
+      if (e != cudaSuccess) {
+        h->xbc_vals = nullptr;
+        return fail(OLB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      }
+    }
     h->inflow.rho = rho;
     for (int a = 0; a < 3; ++a) h->inflow.u[a] = a < h->D ? u[a] : 0.0;
     h->inflow.theta = h->comp ? theta : 1.0;
+    rc = launch_rc(launch_xbc_values(h->aux, h->inflow, h->xbc_vals, h->stream), "x boundary values");
+    if (rc) return rc;
     h->xbc = 1;
     return apply_xbc(h, h->buf[h->cur]);
   }

@@ -187,9 +187,11 @@ int launch_reduce_final(const double* partials, int nslots, double* out, void* s
 struct XInflow {
   double rho, u[3], theta;
 };
-// Refill the x ghost columns: inflow equilibrium on the left, copies of the
+// Inflow value of every plane in storage form (vals: planes elements).
+int launch_xbc_values(const AuxArgs& a, const XInflow& in, void* vals, void* stream);
+// Refill the x ghost columns: the inflow values on the left, copies of the
 // last column on the right (every plane, every padded row).
-int launch_xbc(const AuxArgs& a, void* state, const XInflow& in, void* stream);
+int launch_xbc(const AuxArgs& a, void* state, const void* vals, void* stream);
 // Per-block partial sums of |curl u|^2 (slot 0 of NRED per block) of the
 // velocity u [D][n] (FP64), fourth-order central differences of spacing dx.
 int launch_enstrophy(const AuxArgs& a, const double* u, double dx, double* partials, int grid, void* stream);
