@@ -99,3 +99,16 @@ def test_strerror(olb):
     L = olb.lib()
     for c in range(0, -9, -1):
         assert L.olb_strerror(c)
+
+
+def test_null_arguments_are_rejected_before_any_device_work(olb):
+    """Entry points check their pointers first: no GPU is touched here."""
+    import ctypes as C
+    L = olb.lib()
+    u = (C.c_double * 3)(0.1, 0.0, 0.0)
+    assert L.olb_set_x_boundary(None, 1, 1.0, u, 1.0) == -1
+    assert L.olb_fp64_fma_peak(None, None) == -1
+    assert L.olb_step(None, 1) == -1
+    assert L.olb_get_state(None, None, 0, 0) == -1
+    assert L.olb_set_state(None, None, 0, 0) == -1
+    assert L.olb_destroy(None) == -1
