@@ -8,5 +8,7 @@ the product.
 
 ``sllbm.strain_dissipation`` is a builder's estimator (no formula in the
 paper); it is pinned by the analytic strain of the 3D Taylor-Green vortex
-(tests/test_oracle_step.py).
+(tests/test_oracle_step.py).  ``glc`` holds the paper's cell-wise
+Gauss-Lobatto-Chebyshev interpolation (tests/test_oracle_glc.py); the CUDA
+library does not implement it yet.
 """
