@@ -112,6 +112,18 @@ int olb_velocity_set_info(int velocity_set, int* Q, int* D, double* cs,
 /* Copy the velocity set's abscissae (Q x D, row-major, unscaled) and weights. */
 int olb_velocity_set_table(int velocity_set, double* xi, double* w);
 
+/* Stencils of the cell-wise interpolation on Gauss-Lobatto-Chebyshev points
+ * (Sec. 3, the paper's streaming): an axis of C cells of width H carries C p
+ * nodes, node c p + k at H (c + (1 - cos(pi k / p)) / 2).  For a departure
+ * point displaced by -shift cell widths, the node of residue k (k = 0..p-1)
+ * reads the p + 1 nodes first[k] + m (m = 0..p, relative to the node) with
+ * the Lagrange weights W[k (p + 1) + m] of the cell that contains the
+ * departure point.  first: p ints, W: p (p + 1) doubles, caller-owned.  No
+ * GPU needed.  OLB_EINVAL for p outside 1..OLB_GLC_MAX_P, a non-finite shift
+ * or a null output.  (The step kernels do not use this layout yet.) */
+#define OLB_GLC_MAX_P 8
+int olb_glc_stencil(int p, double shift, int* first, double* W);
+
 /* Create a simulation.  hermite_order N in {2,3,4} (Sec. 3); tau > 1/2 the
  * BGK relaxation time (ignored when compressible: tau(P) from opt->mu); dt > 0.
  * Allocates the two population buffers, the per-CTA scratch and the reduction

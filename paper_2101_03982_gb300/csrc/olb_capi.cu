@@ -624,6 +624,27 @@ int olb_velocity_set_table(int velocity_set, double* xi, double* w) {
   return OLB_OK;
 }
 
+int olb_glc_stencil(int p, double shift, int* first, double* W) {
+  if (p < 1 || p > OLB_GLC_MAX_P) return fail(OLB_EINVAL, "GLC order p must be in 1..8");
+  if (!std::isfinite(shift)) return fail(OLB_EINVAL, "shift must be finite");
+  if (!first || !W) return fail(OLB_EINVAL, "null output");
+  double z[OLB_GLC_MAX_P + 1];
+  for (int m = 0; m <= p; ++m) z[m] = 0.5 * (1.0 - std::cos(M_PI * m / p));
+  for (int k = 0; k < p; ++k) {
+    // departure point of the node with local coordinate z[k], in cell widths
+    const double xl = z[k] - shift;
+    const double d = std::floor(xl), zeta = xl - d;
+    first[k] = (int)d * p - k;
+    for (int m = 0; m <= p; ++m) {
+      double prod = 1.0;
+      for (int l = 0; l <= p; ++l)
+        if (l != m) prod *= (zeta - z[l]) / (z[m] - z[l]);
+      W[k * (p + 1) + m] = prod;
+    }
+  }
+  return OLB_OK;
+}
+
 int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double tau, double dt,
                const olb_options* opt_in, olb_handle* out) {
   if (!grid || !out) return fail(OLB_EINVAL, "null grid or output handle");

@@ -77,6 +77,7 @@ def lib():
             "olb_equilibrium_vjp": (i, [vp, vp, vp, vp, vp, vp, i]),
             "olb_fp64_fma_peak": (i, [vp, dp]),
             "olb_set_x_boundary": (i, [vp, i, d, dp, d]),
+            "olb_glc_stencil": (i, [i, d, ip, dp]),
             "olb_strerror": (ctypes.c_char_p, [i]),
             "olb_last_error": (ctypes.c_char_p, []),
         }
@@ -108,6 +109,15 @@ def fp64_fma_peak(stream=None):
     out = ctypes.c_double()
     _check(lib().olb_fp64_fma_peak(stream, ctypes.byref(out)))
     return out.value
+
+
+def glc_stencil(p, shift):
+    """Per-residue (first (p,), W (p, p+1)) of the cell-wise GLC interpolation."""
+    first = np.zeros(p, dtype=np.int32)
+    W = np.zeros((p, p + 1))
+    _check(lib().olb_glc_stencil(int(p), float(shift), first.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 W.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return first, W
 
 
 def velocity_set_table(name):

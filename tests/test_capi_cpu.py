@@ -112,3 +112,26 @@ def test_null_arguments_are_rejected_before_any_device_work(olb):
     assert L.olb_get_state(None, None, 0, 0) == -1
     assert L.olb_set_state(None, None, 0, 0) == -1
     assert L.olb_destroy(None) == -1
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("shift", [0.0, 0.37, -0.61, 1.45, -2.2])
+def test_glc_stencils_equal_the_oracle(olb, p, shift):
+    """The library's cell-wise GLC stencils (host code, no GPU) against the
+    oracle's, which are pinned on their own (tests/test_oracle_glc.py)."""
+    from oracle import glc as G
+    first, W = olb.glc_stencil(p, shift)
+    for k, (f0, w) in enumerate(G.residue_stencils(p, shift)):
+        assert first[k] == f0
+        assert np.abs(W[k] - w).max() < 1e-14
+
+
+def test_glc_stencil_argument_checks(olb):
+    import ctypes as C
+    L = olb.lib()
+    first = (C.c_int * 8)()
+    W = (C.c_double * 72)()
+    assert L.olb_glc_stencil(0, 0.1, first, W) == -1
+    assert L.olb_glc_stencil(9, 0.1, first, W) == -1
+    assert L.olb_glc_stencil(3, float("inf"), first, W) == -1
+    assert L.olb_glc_stencil(3, 0.1, None, W) == -1
