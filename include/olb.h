@@ -195,7 +195,8 @@ int olb_set_populations(olb_handle h, const double* f, int on_device);
  * periodic again (every ghost copy rewritten from the interior).  OLB_EINVAL
  * for another kind, a null u, rho <= 0 or a non-finite value (theta <= 0 when
  * compressible).  The adjoint and the tape (olb_tape_*, olb_adjoint_step)
- * return OLB_EUNSUPPORTED while kind 1 is set. */
+ * return OLB_EUNSUPPORTED while kind 1 is set; olb_enstrophy keeps its
+ * periodic differences in x. */
 int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, double theta);
 
 /* Raw stored state (checkpoint): exactly olb_state_bytes() bytes, the
