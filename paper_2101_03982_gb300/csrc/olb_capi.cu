@@ -1172,8 +1172,8 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
     return apply_xbc(h, h->buf[h->cur]);
   }
   if (!h->xbc) return OLB_OK;
-  // back to periodic: rewrite every ghost copy from the interior
-  h->xbc = 0;
+  // back to periodic: rewrite every ghost copy from the interior (the handle
+  // stays non-periodic if that fails)
   const size_t bytes = (size_t)h->planes * h->nnodes * h->elem;
   void* tmp = nullptr;
   rc = dev_alloc(h, &tmp, bytes);
@@ -1182,7 +1182,9 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
   if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], tmp, h->stream), "scatter");
   cudaFreeAsync(tmp, h->stream);
   int r2 = stream_sync(h, 0);
-  return rc == OLB_OK ? r2 : rc;
+  if (rc == OLB_OK) rc = r2;
+  if (rc == OLB_OK) h->xbc = 0;
+  return rc;
 }
 
 int olb_synchronize(olb_handle h, int timeout_ms) {
