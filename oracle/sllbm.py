@@ -29,7 +29,8 @@ T0 = c_s^2 of the set; C_v = 1/(gamma - 1); one step = pull, then collide, and
 the stored state is post-collision; f at t = 0 is the equilibrium of the
 initial fields.
 
-Parity pins: see tests/test_oracle_*.py.  The dissipation estimator
+Parity pins: see tests/test_oracle_*.py (``reductions`` and the gather form
+``step_at_points`` in tests/test_oracle_reductions.py).  The dissipation estimator
 ``strain_dissipation`` is a builder's quantity (no formula in the paper),
 pinned by the analytic strain of the decaying 3D Taylor-Green vortex.
 """
@@ -406,11 +407,6 @@ def init_equilibrium(prm, rho, u, theta=None):
     return f, g
 
 
-def kinetic_energy(u):
-    """k = mean over nodes of |u|^2 / 2 (Sec. 4.2: (2 pi)^-3 integral on the grid)."""
-    return float(0.5 * (np.asarray(u) ** 2).sum(axis=-1).mean())
-
-
 def strain_dissipation(prm, diag):
     """Builder's estimator: eps = mean 2 nu S:S with S = -Pi_neq / (2 P tau dt).
 
@@ -428,7 +424,12 @@ def strain_dissipation(prm, diag):
 
 
 def reductions(prm, diag):
-    """Global per-step sums: k, rho-weighted k, dissipation estimate, mass, momentum."""
+    """Global per-step sums of the post-streaming moments: k = mean |u|^2 / 2
+    (Sec. 4.2, the mean kinetic energy; on the uniform grid the integral over
+    the box divided by its volume is the node mean), the rho-weighted
+    k_rho = mean rho |u|^2 / 2, the dissipation estimate, the mass sum rho
+    and the momentum sum rho u.  Pinned by closed forms in
+    tests/test_oracle_reductions.py."""
     rho, u = diag["rho"], diag["u"]
     ke = 0.5 * (u ** 2).sum(axis=1)
     return dict(
