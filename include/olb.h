@@ -133,29 +133,55 @@ int olb_glc_stencil(int p, double shift, int* first, double* W);
 int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double tau,
                double dt, const olb_options* opt /* nullable */, olb_handle* out);
 
+/* Release the handle and every device buffer it owns (no counterpart in the paper).
+ * Synchronises the handle's stream first.  OLB_EINVAL for a null handle. */
 int olb_destroy(olb_handle h);
 
 /* Q, planes (Q or 2Q), nodes, dimension and the storage element size in bytes. */
 int olb_shape(olb_handle h, int* Q, int* planes, size_t* nodes, int* dim, int* elem_bytes);
 
-/* Per-velocity stencil table used by the pull: m0[Q*3] (first support point
- * per axis, grid units) and W[Q*3*(p+1)] Lagrange weights (FP64). */
+/* Per-velocity stencil table of the pull (Sec. 3, Eq. sl_streaming: the
+ * population of velocity i is interpolated at the departure point x - xi_i dt,
+ * i.e. at the offset delta = -xi_{i,a} dt / dx grid units along axis a):
+ * m0[Q*3] (first support point per axis, grid units, row-major [i][a]) and
+ * W[Q*3*(p+1)] the Lagrange weights of the p + 1 points m0 .. m0 + p at delta
+ * (FP64, [i][a][j]).  Caller-owned host arrays of those sizes (either may be
+ * NULL).  An axis with xi_{i,a} = 0 has m0 = 0 and the weights of delta = 0
+ * (a Kronecker delta).  OLB_EINVAL for a null handle. */
 int olb_stencil(olb_handle h, int* m0, double* W);
 
-/* f = f^eq(rho, u, theta) (and g = theta (2 C_v - D) f^eq): rho [n], u [D][n],
- * theta [n] or NULL (= 1).  FP64 fields. */
+/* Initial state from macroscopic fields.  The paper does not state how the
+ * populations start; this call implements the reading f_i = f_i^eq(rho, u,
+ * theta), the Hermite equilibrium of order N of Sec. 3 and Appendix A (and
+ * g_i = theta (2 C_v - D) f_i^eq, the compressible model's g equilibrium of
+ * Sec. 3), with no non-equilibrium part.  rho [n], u [D][n], theta [n] or
+ * NULL (= 1): FP64 fields in the layout above.  The result is rounded to the
+ * storage type (shifted where the storage is).  OLB_EINVAL for a null handle,
+ * rho or u; OLB_ENOMEM when a host-field staging buffer cannot be allocated. */
 int olb_init_fields(olb_handle h, const double* rho, const double* u, const double* theta,
                     int on_device);
 
-/* Advance n >= 0 steps (pull, then collide).  Asynchronous on the handle's
- * stream.  A step whose running count (since olb_create) is a multiple of
+/* Advance n >= 0 steps of the semi-Lagrangian LBE (Sec. 3): each step pulls
+ * every population from its departure point (Eq. sl_streaming), forms the
+ * moments, the order-N Hermite equilibrium (Appendix A) and relaxes by BGK
+ * (the LBE of Sec. 3; compressible: tau = mu/(c_s^2 dt P) + 1/2 per node).
+ * The stored state is the post-collision one (one step = pull, then
+ * collide).  Asynchronous on the handle's stream; OLB_EINVAL for n < 0,
+ * OLB_ECUDA when a launch fails, OLB_ETIMEOUT when an earlier step gave up
+ * waiting for a staging copy and no new state has been written since.  A step whose running count (since olb_create) is a multiple of
  * log_every also leaves per-CTA FP64 partial sums of the global reductions,
  * which olb_reductions() combines.  Device memory: the handle keeps each
  * plane with ghost layers of periodic copies around the interior, which the
  * step refreshes as it writes. */
 int olb_step(olb_handle h, int n);
 
-/* rho [n], u [D][n], theta [n] (nullable) of the stored post-collision state. */
+/* Moments of the stored post-collision state: rho = sum_i f_i and
+ * rho u = sum_i xi_i f_i (Sec. 3, density and momentum moments), and for a
+ * compressible state theta from 2 rho C_v theta = sum_i |xi_i - u|^2 f_i / T0
+ * + sum_i g_i (Sec. 3, temperature relation; T0 = 1).  BGK conserves these, so
+ * they equal the moments of the pulled populations of the last step.  Outputs
+ * rho [n], u [D][n], theta [n] (nullable; 1 for isothermal states) in FP64,
+ * host or device per on_device.  OLB_EINVAL for a null handle, rho or u. */
 int olb_moments(olb_handle h, double* rho, double* u, double* theta, int on_device);
 
 /* Global sums of the most recent step when that step accumulated them (else
@@ -181,7 +207,12 @@ int olb_kinetic_energy(olb_handle h, double* k, double* dissipation);
  * OLB_ENONFINITE if the result is not finite. */
 int olb_enstrophy(olb_handle h, double* enstrophy);
 
-/* Populations as FP64 unshifted values, [planes][n]. */
+/* The populations f_i (planes Q..2Q-1: g_i) of the stored post-collision
+ * state, the unknowns of the LBE of Sec. 3, as FP64 unshifted values in the
+ * compact layout [planes][nz][ny][nx] (no ghost layers).  get converts from
+ * the storage type exactly; set rounds to it (after removing the shift
+ * w_i rho0) and refreshes the ghost layers.  OLB_EINVAL for a null handle or
+ * array. */
 int olb_get_populations(olb_handle h, double* f, int on_device);
 int olb_set_populations(olb_handle h, const double* f, int on_device);
 
@@ -211,8 +242,22 @@ size_t olb_state_bytes(olb_handle h);
 int olb_get_state(olb_handle h, void* buf, size_t bytes, int on_device);
 int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);
 
-/* Wait for the handle's stream, polling with a bound of timeout_ms (<= 0: no bound). */
+/* Wait for the handle's stream, polling with a bound of timeout_ms (<= 0: no bound),
+ * then check the device error flag of the step kernels (no counterpart in the paper).
+ * OLB_ETIMEOUT when the bound ran out or a step gave up waiting for a staging copy. */
 int olb_synchronize(olb_handle h, int timeout_ms);
+
+/* Bound of the step kernels' waits for their staging copies, in polls of the
+ * copy's barrier (no counterpart in the paper; a diagnostic of the error path).
+ * polls < 0 restores the default (2^24 polls, far beyond any copy's latency);
+ * polls = 0 makes every step give up at its first wait, so that a test can
+ * check the error path without a fault: the kernel raises the device error
+ * flag, waits (with the default bound) for the copies it has in flight and
+ * returns.  The next call that checks the flag returns OLB_ETIMEOUT; the
+ * state is then invalid, and steps and reads return OLB_ETIMEOUT until a new
+ * state is written (olb_init_fields, olb_set_populations, olb_set_state).
+ * OLB_EINVAL for a null handle. */
+int olb_set_wait_polls(olb_handle h, long long polls);
 
 /* ---- Adjoint of the isothermal step (vector-Jacobian products) ----------------------------
  * The paper defines the forward step only (Sec. 3: pull by Eq. sl_streaming, BGK with the
@@ -259,15 +304,22 @@ int olb_equilibrium_vjp(olb_handle h, const double* rho, const double* u, const 
  * so the call allocates nothing.
  *   populations: device pointer, [Q][nz][ny][nx] storage values (the layout of
  *                olb_get_state for an isothermal state: shifted by w_i rho0
- *                unless storage is OLB_FP64);
+ *                unless storage is OLB_FP64).  Only these Q planes of f are
+ *                read: for a compressible state pass its first Q planes; its
+ *                g planes and temperature are not used (k_rho is mean
+ *                rho |u|^2 / 2, which needs neither);
+ *   rho0:        the reference density the state was shifted with (the
+ *                handle's rho0 option); ignored for OLB_FP64;
  *   out:         device pointer to 8 doubles, filled like olb_reductions()
  *                with out[2] = NaN (no dissipation estimate without a step);
  *   stream:      cudaStream_t or NULL; the call only enqueues work on it.
  * Grids of more than OLB_NOALLOC_MAX_BLOCKS * OLB_NOALLOC_NODES_PER_BLOCK nodes
  * are rejected with OLB_EBOUNDS.  The first call on a device looks up the
  * array's device address with that device current; make that first call
- * before any stream capture.  All calls share the array and each overwrites
- * the slots it uses, so calls whose kernels overlap on the GPU race. */
+ * before any stream capture.  The address is cached per device together with
+ * the identity of the device's context; after a cudaDeviceReset the next call
+ * looks it up again.  All calls share the array and each overwrites the slots
+ * it uses, so calls whose kernels overlap on the GPU race. */
 #define OLB_NOALLOC_MAX_BLOCKS 2048
 #define OLB_NOALLOC_NODES_PER_BLOCK 65536
 int olb_state_sums_noalloc(int velocity_set, const olb_grid* grid, int storage, double cs_scale,

@@ -54,6 +54,7 @@ struct olb_ctx {
   int force_generic = 0;
   long long step_count = 0;
   int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
+  int state_bad = 0;       // 1: a step gave up waiting for a staging copy; no valid state since
   int xbc = 0;             // 1: non-periodic x (inflow / zero-gradient outflow ghost columns)
   XInflow inflow{};
   void* xbc_vals = nullptr;  // inflow value per plane, storage form
@@ -330,14 +331,32 @@ int build_maps(olb_ctx* h) {
   return OLB_OK;
 }
 
-// Device error flag set by a step kernel whose bounded wait ran out.
+// Device error flag set by a step kernel whose bounded wait ran out.  The
+// flag is moved to the handle (state_bad) and cleared on the device; the state
+// stays invalid until a writer of a whole state (init, set_populations,
+// set_state) runs.
 int check_err(olb_ctx* h) {
   int v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "error flag");
-  if (v) return fail(OLB_ETIMEOUT, "a step kernel gave up waiting for a staging copy; the state is invalid");
+  if (v) {
+    h->state_bad = 1;
+    e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "error flag reset");
+  }
+  if (h->state_bad)
+    return fail(OLB_ETIMEOUT, "a step kernel gave up waiting for a staging copy; the state is invalid "
+                              "until a new one is written");
   return OLB_OK;
+}
+
+// A writer of a whole state starts a valid history: clear both error flags
+// (stream-ordered after any step that ran before it).
+int clear_err(olb_ctx* h) {
+  h->state_bad = 0;
+  cudaError_t e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
+  return e == cudaSuccess ? OLB_OK : cuda_fail(e, "error flag reset");
 }
 
 int set_device(olb_ctx* h) {
@@ -815,6 +834,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   a.scratch = h->scratch;
   a.partials = h->partials;
   a.err = h->err_dev;
+  a.wait_polls = 1LL << 24;
   {
     int rcm = build_maps(h);
     if (rcm != OLB_OK) {
@@ -886,6 +906,8 @@ int olb_init_fields(olb_handle h, const double* rho, const double* u, const doub
   if (!h || !rho || !u) return fail(OLB_EINVAL, "null handle or field");
   int rc = set_device(h);
   if (rc) return rc;
+  rc = clear_err(h);
+  if (rc) return rc;
   const size_t n = (size_t)h->nnodes;
   const double *dr = rho, *du = u, *dth = theta;
   void* tmp = nullptr;
@@ -914,6 +936,9 @@ int olb_init_fields(olb_handle h, const double* rho, const double* u, const doub
 int olb_step(olb_handle h, int n) {
   if (!h) return fail(OLB_EINVAL, "null handle");
   if (n < 0) return fail(OLB_EINVAL, "negative step count");
+  if (h->state_bad)
+    return fail(OLB_ETIMEOUT, "the state is invalid after a step gave up waiting for a staging copy; "
+                              "write a new state first");
   int rc = set_device(h);
   if (rc) return rc;
   StepLaunch L = base_launch(h);
@@ -1059,6 +1084,8 @@ int olb_set_populations(olb_handle h, const double* f, int on_device) {
   if (!h || !f) return fail(OLB_EINVAL, "null handle or buffer");
   int rc = set_device(h);
   if (rc) return rc;
+  rc = clear_err(h);
+  if (rc) return rc;
   const size_t bytes = (size_t)h->planes * h->nnodes * sizeof(double);
   const double* d = f;
   void* tmp = nullptr;
@@ -1117,6 +1144,8 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
   if (!h || !buf) return fail(OLB_EINVAL, "null handle or buffer");
   if (bytes != olb_state_bytes(h)) return fail(OLB_EINVAL, "state size mismatch");
   int rc = set_device(h);
+  if (rc) return rc;
+  rc = clear_err(h);
   if (rc) return rc;
   const void* d = buf;
   void* tmp = nullptr;
@@ -1185,6 +1214,12 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
   if (rc == OLB_OK) rc = r2;
   if (rc == OLB_OK) h->xbc = 0;
   return rc;
+}
+
+int olb_set_wait_polls(olb_handle h, long long polls) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  h->args.wait_polls = polls < 0 ? (1LL << 24) : polls;
+  return OLB_OK;
 }
 
 int olb_synchronize(olb_handle h, int timeout_ms) {

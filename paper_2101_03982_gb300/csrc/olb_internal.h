@@ -90,6 +90,7 @@ struct StepArgs {
   void* scratch;        // per-CTA staging of pulled populations
   double* partials;     // per-CTA reduction partials [grid][NRED]
   int* err;             // device error flag (1: a bounded wait ran out)
+  long long wait_polls; // bound of the waits for staging copies (polls of the barrier)
   Padded pad;
   int nt[3];            // tiles per axis
   int ntiles;

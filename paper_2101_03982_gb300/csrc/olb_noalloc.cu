@@ -12,9 +12,11 @@
 // the final kernel reads it, so nothing has to start at zero, but calls whose
 // kernels overlap on the GPU (different streams, no ordering between them)
 // race on the array.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <mutex>
@@ -32,9 +34,37 @@ constexpr int NA_RED = 8;
 static __device__ __align__(256) double g_noalloc_partials[NA_MAX_BLOCKS * NA_RED];
 
 // Device address of g_noalloc_partials per device (the host-side name is only
-// a stand-in), looked up once per device with that device current.
+// a stand-in), looked up with that device current, together with the identity
+// of the context it belongs to: a device reset makes a new context (and loads
+// the module again), so a changed identity means the address is looked up
+// again.
 std::mutex g_mu;
 double* g_addr[64] = {};
+unsigned long long g_ctx_id[64] = {};
+
+// Identity of the calling thread's current context (0 when none or unknown).
+unsigned long long current_ctx_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 template <typename S>
 __device__ __forceinline__ double val(S v);
@@ -145,12 +175,15 @@ extern "C" int olb_state_sums_noalloc(int velocity_set, const olb_grid* grid, in
   double* part = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
+      // first call on this device, or its context changed: (re)load the address
       e = cudaGetSymbolAddress((void**)&g_addr[dev], g_noalloc_partials);
       if (e != cudaSuccess) {
         g_addr[dev] = nullptr;
         return fail(OLB_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
+      g_ctx_id[dev] = current_ctx_id();  // the lookup made the primary context current
     }
     part = g_addr[dev];
   }

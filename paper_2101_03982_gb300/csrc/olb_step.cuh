@@ -159,9 +159,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when the copy did not land within the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (long spin = 0; spin < (1L << 24); ++spin)
+// Bounded wait: false when the copy did not land within `limit` polls (the
+// default bound, 2^24 polls, is far beyond any copy's latency).
+constexpr long long WAIT_POLLS_DEFAULT = 1LL << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long limit = WAIT_POLLS_DEFAULT) {
+  for (long long spin = 0; spin < limit; ++spin)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(NT, 1)
     }
 
     for (int p = 0; p < planes; ++p) {
-      const bool ok = mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u);
+      const bool ok = mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u, a.wait_polls);
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.err, 1);
         mbar_wait_bounded(&bars[buf], (parity >> buf) & 1u);

@@ -432,7 +432,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     if constexpr (L::INPL) {
       for (int k = 0; k < nplan && !failed; ++k) {
         const int plane = sched.plane[wg][k];
-        if (wg_any(wg, !mbar_wait_bounded(bar + cb, (parity >> cb) & 1u))) {
+        if (wg_any(wg, !mbar_wait_bounded(bar + cb, (parity >> cb) & 1u, a.wait_polls))) {
           failed = true;
           break;
         }
@@ -546,7 +546,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     for (int k = 0; k < nplan && !failed; ++k) {
       const int plane = sched.plane[wg][k];
       // every thread of the warpgroup takes the same decision
-      if (wg_any(wg, !mbar_wait_bounded(bar, parity))) {
+      if (wg_any(wg, !mbar_wait_bounded(bar, parity, a.wait_polls))) {
         failed = true;
         break;
       }

@@ -67,6 +67,7 @@ def lib():
             "olb_get_state": (i, [vp, vp, sz, i]),
             "olb_set_state": (i, [vp, vp, sz, i]),
             "olb_synchronize": (i, [vp, i]),
+            "olb_set_wait_polls": (i, [vp, ctypes.c_longlong]),
             "olb_state_sums_noalloc": (i, [i, ctypes.POINTER(Grid), i, d, d, vp, vp, vp]),
             "olb_enstrophy": (i, [vp, dp]),
             "olb_tape_reserve": (i, [vp, i]),
@@ -287,6 +288,10 @@ class Sim:
 
     def synchronize(self, timeout_ms=0):
         _check(lib().olb_synchronize(self._h, int(timeout_ms)))
+
+    def set_wait_polls(self, polls):
+        """Bound of the step kernels' staging waits (< 0: the default; 0: give up at once)."""
+        _check(lib().olb_set_wait_polls(self._h, int(polls)))
 
     # -- adjoint of the isothermal step ----------------------------------------
     @property
