@@ -8,10 +8,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "olb.h"
@@ -71,10 +73,13 @@ struct olb_ctx {
   std::vector<double> W;      // [Q][3][p+1]
   // adjoint: tape of forward states (padded, like buf) and the adjoint buffers
   std::vector<void*> tape;
-  std::vector<TmaMaps> tape_maps;  // m[0] of each slot
+  std::vector<TmaMaps> tape_maps;  // m[0] of each slot (the forward kernel's boxes)
+  std::vector<TmaMaps> tape_amaps; // m[0] of each slot (the adjoint kernel's boxes)
   int tape_len = 0;                // slots holding a recorded state
   void* adj[2] = {nullptr, nullptr};
   TmaMaps adj_maps{};              // m[k] of adj[k]
+  StepInfo ainfo{};                // geometry of the adjoint kernel (the two-phase kernel's)
+  int adj_grid = 0, adj_nt[3] = {0, 0, 0}, adj_ntiles = 0;
   void* adj_scratch = nullptr;
   std::vector<unsigned char> st_refl, st_id;  // reflected and identity stencils
   WgSchedule sched_adj[3]{};       // first step, middle steps, last (pull only)
@@ -165,6 +170,42 @@ void fill_veltab(olb_ctx* h) {
   }
 }
 
+// FP32 copy of the Lagrange weights of one stencil.  Rounded one by one to
+// nearest, FP32 weights sum to 1 + O(1e-8): the pull would then scale every
+// population, and the mass and momentum it carries, by that factor at every
+// step (over 500 steps the kinetic energy of the 3D Taylor-Green vortex in
+// FP32 drifted by up to 1e-4 from the FP64 run).  Here each weight is rounded
+// up or down (staying within one ulp of its FP64 value), choosing among the
+// 2^(p+1) combinations the one whose sum is closest to 1, then whose first and
+// second moments about the departure point are closest to the exact ones; the
+// sums are exact in FP64.
+void nearest_sum_weights_f32(const double* W, const int* m, double delta, int n, float* out) {
+  float lo[MAXP + 1], hi[MAXP + 1];
+  double m1 = 0.0, m2 = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const float f = (float)W[j];
+    lo[j] = (double)f <= W[j] ? f : std::nextafter(f, -INFINITY);
+    hi[j] = (double)f >= W[j] ? f : std::nextafter(f, INFINITY);
+    m1 += W[j] * (m[j] - delta);
+    m2 += W[j] * (m[j] - delta) * (m[j] - delta);
+  }
+  double best[3] = {INFINITY, INFINITY, INFINITY};
+  for (int mask = 0; mask < (1 << n); ++mask) {
+    double s = 0.0, e1 = 0.0, e2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double v = (mask >> j) & 1 ? hi[j] : lo[j];
+      s += v;
+      e1 += v * (m[j] - delta);
+      e2 += v * (m[j] - delta) * (m[j] - delta);
+    }
+    const double c[3] = {std::fabs(s - 1.0), std::fabs(e1 - m1), std::fabs(e2 - m2)};
+    if (c[0] < best[0] || (c[0] == best[0] && (c[1] < best[1] || (c[1] == best[1] && c[2] < best[2])))) {
+      for (int k = 0; k < 3; ++k) best[k] = c[k];
+      for (int j = 0; j < n; ++j) out[j] = (mask >> j) & 1 ? hi[j] : lo[j];
+    }
+  }
+}
+
 template <typename C, int P1>
 void fill_stentab_p(olb_ctx* h) {
   h->stentab.assign(sizeof(StencilTab<C, P1>), 0);
@@ -175,9 +216,74 @@ void fill_stentab_p(olb_ctx* h) {
     for (int a = 0; a < h->D; ++a) {
       if (h->set.xi[i][a] != 0.0) act |= 1 << a;
       t->m0[i][a] = h->m0[i * 3 + a];
-      for (int j = 0; j <= p; ++j) t->W[i][a][j] = (C)h->W[(i * 3 + a) * (p + 1) + j];
+      const double* Wd = &h->W[(i * 3 + a) * (p + 1)];
+      if constexpr (std::is_same<C, float>::value) {
+        int mm[MAXP + 1];
+        for (int j = 0; j <= p; ++j) mm[j] = h->m0[i * 3 + a] + j;
+        const double delta = -h->set.xi[i][a] * h->dt / h->grid.dx;
+        nearest_sum_weights_f32(Wd, mm, delta, p + 1, t->W[i][a]);
+      } else {
+        for (int j = 0; j <= p; ++j) t->W[i][a][j] = (C)Wd[j];
+      }
     }
     t->active[i] = act;
+  }
+}
+
+// Inverse of the D x D block of M (the rest zero).
+void inverse_block(const double M[3][3], int D, double inv[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) inv[a][b] = 0.0;
+  if (D == 2) {
+    const double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    inv[0][0] = M[1][1] / det;
+    inv[0][1] = -M[0][1] / det;
+    inv[1][0] = -M[1][0] / det;
+    inv[1][1] = M[0][0] / det;
+    return;
+  }
+  const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      // adjugate: the cofactor of (b, a), signs from the cyclic index order
+      const int a1 = (b + 1) % 3, a2 = (b + 2) % 3, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+      inv[a][b] = (M[a1][b1] * M[a2][b2] - M[a1][b2] * M[a2][b1]) / det;
+    }
+}
+
+// Correction g of the FP32 equilibrium velocity u^ = (I + diag(g)) u^0,
+// u^0 = j fl(1/c_s) / rho (see uhat_of in olb_step.cuh).  The collision keeps the momentum j when the equilibrium's
+// momentum, computed with the FP32 tables it is built from, is what the BGK
+// form needs:
+//  * isothermal, (1 - fl(1/tau)) f + fl(w/tau) e:  rho M_wt u^ = fl(1/tau) j
+//    with M_wt = sum_i fl(w_i/tau) xi_i (xi_i/c_s), so
+//    I + diag(g) = fl(1/tau) M_wt^-1 / fl(1/c_s);
+//  * compressible, f - (f - w e)/tau:  rho M_w u^ = j with
+//    M_w = sum_i fl(w_i) xi_i (xi_i/c_s), so I + diag(g) = M_w^-1 / fl(1/c_s).
+// The products and sums of the FP32 table values are exact in FP64.
+void fill_uhat_fix(olb_ctx* h) {
+  const auto* t = reinterpret_cast<const VelTab<float>*>(h->veltab.data());
+  const int D = h->D;
+  double Mw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Mt[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int i = 0; i < h->Q; ++i)
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        const double xx = (double)t->xi[i][a] * (double)t->xih[i][b];
+        Mw[a][b] += (double)t->w[i] * xx;
+        Mt[a][b] += (double)t->wt[i] * xx;
+      }
+  double iw[3][3], it[3][3];
+  inverse_block(Mw, D, iw);
+  inverse_block(Mt, D, it);
+  const double ics = (double)(float)(1.0 / h->cs);
+  const double itau = (double)(float)(1.0 / h->tau);
+  // the tables are symmetric under the reflection of every axis, so M is
+  // diagonal (its off-diagonal sums cancel exactly): only the diagonal is kept
+  for (int a = 0; a < 3; ++a) {
+    h->args.f_g[a] = (!h->comp && a < D) ? (float)(itau * it[a][a] / ics - 1.0) : 0.f;
+    h->args.f_gc[a] = a < D ? (float)(iw[a][a] / ics - 1.0) : 0.f;
   }
 }
 
@@ -244,7 +350,9 @@ void layout_padding(olb_ctx* h) {
 
 // Planes of each warpgroup of the two-phase kernel: longest processing time
 // first, with a plane's cost from the passes its stencil needs.
-static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSchedule* out) {
+// kmax > 0 caps the planes of a warpgroup (the register-resident kernel holds
+// at most kmax planes per warpgroup); the caller guarantees planes <= nwg kmax.
+static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSchedule* out, int kmax = 0) {
   WgSchedule& S = *out;
   std::memset(&S, 0, sizeof(S));
   if (nwg < 1) nwg = 1;
@@ -252,9 +360,12 @@ static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSc
   double load[4] = {0, 0, 0, 0};
   std::vector<int> lists[4];
   for (const auto& cp : cost) {
-    int best = 0;
-    for (int w = 1; w < nwg; ++w)
-      if (load[w] < load[best]) best = w;
+    int best = -1;
+    for (int w = 0; w < nwg; ++w) {
+      if (kmax > 0 && (int)lists[w].size() >= kmax) continue;
+      if (best < 0 || load[w] < load[best]) best = w;
+    }
+    if (best < 0) best = 0;
     load[best] += cp.first;
     lists[best].push_back(cp.second);
   }
@@ -279,7 +390,7 @@ static double plane_cost(const olb_ctx* h, int i) {
 static void build_schedule(olb_ctx* h) {
   std::vector<std::pair<double, int>> cost;
   for (int p = 0; p < h->planes; ++p) cost.push_back({plane_cost(h, p % h->Q), p});
-  lpt_schedule(h->info.wg, cost, &h->sched);
+  lpt_schedule(h->info.wg, cost, &h->sched, h->info.kmax);
 }
 
 namespace {
@@ -298,7 +409,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 4D tiled descriptors (x, y, z, plane) of one padded buffer of `nplanes`
 // planes, one per staged box shape.
-int encode_maps(olb_ctx* h, void* buffer, int nplanes, CUtensorMap out[4]) {
+int encode_maps(olb_ctx* h, void* buffer, int nplanes, CUtensorMap out[4], const StepInfo& g) {
   auto enc = encode_fn();
   if (!enc) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled is not available");
   CUtensorMapDataType dt;
@@ -314,8 +425,8 @@ int encode_maps(olb_ctx* h, void* buffer, int nplanes, CUtensorMap out[4]) {
                                  (cuuint64_t)P.plane * h->elem};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   for (int v = 0; v < 4; ++v) {
-    const cuuint32_t box[4] = {(cuuint32_t)h->info.bxw, (cuuint32_t)((v & 1) ? h->info.by : h->info.ty),
-                               (cuuint32_t)((v & 2) ? h->info.bz : h->info.tz), 1};
+    const cuuint32_t box[4] = {(cuuint32_t)g.bxw, (cuuint32_t)((v & 1) ? g.by : g.ty),
+                               (cuuint32_t)((v & 2) ? g.bz : g.tz), 1};
     CUresult r = enc(&out[v], dt, 4, buffer, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(OLB_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
@@ -325,7 +436,7 @@ int encode_maps(olb_ctx* h, void* buffer, int nplanes, CUtensorMap out[4]) {
 
 int build_maps(olb_ctx* h) {
   for (int b = 0; b < 2; ++b) {
-    const int rc = encode_maps(h, h->buf[b], h->planes, h->maps.m[b]);
+    const int rc = encode_maps(h, h->buf[b], h->planes, h->maps.m[b], h->info);
     if (rc) return rc;
   }
   return OLB_OK;
@@ -470,10 +581,12 @@ void fill_adj_tabs_p(olb_ctx* h) {
   auto* r = reinterpret_cast<StencilTab<C, P1>*>(h->st_refl.data());
   auto* id = reinterpret_cast<StencilTab<C, P1>*>(h->st_id.data());
   const int p = h->p;
+  const auto* f = reinterpret_cast<const StencilTab<C, P1>*>(h->stentab.data());
   for (int i = 0; i < h->Q; ++i) {
     for (int a = 0; a < 3; ++a) {
       r->m0[i][a] = -h->m0[i * 3 + a] - p;
-      for (int j = 0; j <= p; ++j) r->W[i][a][j] = (C)h->W[(i * 3 + a) * (p + 1) + (p - j)];
+      // the forward table's own weights reversed: the exact transpose of its pull
+      for (int j = 0; j <= p; ++j) r->W[i][a][j] = f->W[i][a][p - j];
       id->m0[i][a] = 0;
       id->W[i][a][0] = (C)1;
     }
@@ -496,6 +609,21 @@ int adj_prepare(olb_ctx* h) {
     return fail(OLB_EUNSUPPORTED, "the adjoint is built for FP64 and FP32 storage");
   if (h->info.wg == 0 || (h->p != 3 && h->p != 4))
     return fail(OLB_EUNSUPPORTED, "the adjoint needs the two-phase kernel (p = 3 or 4, automatic kernel choice)");
+  // geometry of the adjoint kernel: the two-phase kernel's tile, boxes and grid
+  if (step_info(h->D, h->p, h->storage, h->comp, h->Q, h->N, 2, &h->ainfo) != 0 || h->ainfo.wg == 0 ||
+      h->ainfo.ctas_per_sm < 1)
+    return fail(OLB_EUNSUPPORTED, "the adjoint kernel is not built for this configuration");
+  {
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    h->adj_nt[0] = (h->grid.n[0] + h->ainfo.tx - 1) / h->ainfo.tx;
+    h->adj_nt[1] = (h->grid.n[1] + h->ainfo.ty - 1) / h->ainfo.ty;
+    h->adj_nt[2] = (h->grid.n[2] + h->ainfo.tz - 1) / h->ainfo.tz;
+    h->adj_ntiles = h->adj_nt[0] * h->adj_nt[1] * h->adj_nt[2];
+    long long g = (long long)sms * h->ainfo.ctas_per_sm;
+    h->adj_grid = (int)(g > h->adj_ntiles ? h->adj_ntiles : g);
+  }
   // the reflected stencil must stay inside the ghost layers
   for (int i = 0; i < h->Q; ++i)
     for (int a = 0; a < h->D; ++a) {
@@ -512,11 +640,11 @@ int adj_prepare(olb_ctx* h) {
     cudaError_t e = cudaMalloc(&h->adj[k], bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->adj[k], 0, bytes, h->stream);
     if (e != cudaSuccess) return fail(OLB_ENOMEM, "adjoint buffers: " + std::string(cudaGetErrorString(e)));
-    const int rc = encode_maps(h, h->adj[k], h->Q, h->adj_maps.m[k]);
+    const int rc = encode_maps(h, h->adj[k], h->Q, h->adj_maps.m[k], h->ainfo);
     if (rc) return rc;
   }
   if (!h->adj_scratch) {
-    const size_t sb = (size_t)h->step_grid * 2 * h->Q * h->info.tile * adj_elem(h);
+    const size_t sb = (size_t)h->adj_grid * 2 * h->Q * h->ainfo.tile * adj_elem(h);
     cudaError_t e = cudaMalloc(&h->adj_scratch, sb);
     if (e != cudaSuccess) return fail(OLB_ENOMEM, "adjoint staging: " + std::string(cudaGetErrorString(e)));
   }
@@ -529,9 +657,15 @@ int adj_prepare(olb_ctx* h) {
     mid.push_back({c, h->Q + i});
     last.push_back({c, h->Q + i});
   }
-  lpt_schedule(h->info.wg, first, &h->sched_adj[0]);
-  lpt_schedule(h->info.wg, mid, &h->sched_adj[1]);
-  lpt_schedule(h->info.wg, last, &h->sched_adj[2]);
+  lpt_schedule(h->ainfo.wg, first, &h->sched_adj[0]);
+  lpt_schedule(h->ainfo.wg, mid, &h->sched_adj[1]);
+  lpt_schedule(h->ainfo.wg, last, &h->sched_adj[2]);
+  // forward-state maps of the tape slots made before the adjoint was prepared
+  for (size_t s = h->tape_amaps.size(); s < h->tape.size(); ++s) {
+    h->tape_amaps.emplace_back();
+    const int rc = encode_maps(h, h->tape[s], h->planes, h->tape_amaps.back().m[0], h->ainfo);
+    if (rc) return rc;
+  }
   h->adj_ready = 1;
   return OLB_OK;
 }
@@ -548,8 +682,11 @@ int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, cons
   L.a.planes = 2 * h->Q;
   L.a.reduce = 0;
   L.a.mode = mode;
+  for (int k = 0; k < 3; ++k) L.a.nt[k] = h->adj_nt[k];
+  L.a.ntiles = h->adj_ntiles;
+  L.grid = h->adj_grid;
   TmaMaps M;
-  std::memcpy(M.m[0], slot >= 0 ? h->tape_maps[slot].m[0] : h->adj_maps.m[in], sizeof(M.m[0]));
+  std::memcpy(M.m[0], slot >= 0 ? h->tape_amaps[slot].m[0] : h->adj_maps.m[in], sizeof(M.m[0]));
   std::memcpy(M.m[1], h->adj_maps.m[in], sizeof(M.m[1]));
   L.stentab2 = st2.data();
   L.maps = &M;
@@ -591,8 +728,13 @@ int tape_grow(olb_ctx* h, int nslots) {
     }
     h->tape.push_back(p);
     h->tape_maps.emplace_back();
-    const int rc = encode_maps(h, p, h->planes, h->tape_maps.back().m[0]);
+    int rc = encode_maps(h, p, h->planes, h->tape_maps.back().m[0], h->info);
     if (rc) return rc;
+    if (h->adj_ready) {
+      h->tape_amaps.emplace_back();
+      rc = encode_maps(h, p, h->planes, h->tape_amaps.back().m[0], h->ainfo);
+      if (rc) return rc;
+    }
   }
   return OLB_OK;
 }
@@ -682,7 +824,8 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   if (!(opt.cs_scale > 0.0) || !std::isfinite(opt.cs_scale)) return fail(OLB_EINVAL, "cs_scale must be positive");
   if (!(opt.rho0 > 0.0)) return fail(OLB_EINVAL, "rho0 must be positive");
   if (opt.log_every < 1) return fail(OLB_EINVAL, "log_every must be >= 1");
-  if (opt.kernel < 0 || opt.kernel > 1) return fail(OLB_EINVAL, "kernel must be 0 (automatic) or 1 (single-role)");
+  if (opt.kernel < 0 || opt.kernel > 3)
+    return fail(OLB_EINVAL, "kernel must be 0 (automatic), 1 (single-role), 2 (two-phase) or 3 (register-resident)");
 
   VelocitySet vs;
   if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
@@ -712,7 +855,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->comp = opt.compressible ? 1 : 0;
   h->allow_inexact = opt.allow_inexact;
   h->log_every = opt.log_every;
-  h->force_generic = opt.kernel == 1;
+  h->force_generic = opt.kernel;  // kernel mode: 0 automatic, 1 single-role, 2 two-phase, 3 register-resident
   h->tau = tau;
   h->dt = dt;
   h->gamma = opt.gamma;
@@ -760,6 +903,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   } else {
     fill_veltab<float>(h);
     fill_stentab<float>(h);
+    fill_uhat_fix(h);
   }
 
   build_schedule(h);
@@ -811,7 +955,8 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
 
   const size_t cbytes = h->storage == OLB_FP64 ? 8 : 4;
   const size_t state_bytes = (size_t)h->planes * h->pad.plane * h->elem;
-  const size_t scratch_bytes = (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
+  // the register-resident kernel (kmax > 0) stages nothing in global memory
+  const size_t scratch_bytes = h->info.kmax > 0 ? 256 : (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
   for (int k = 0; k < 2; ++k) {
     e = cudaMalloc(&h->buf[k], state_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[k], 0, state_bytes, h->stream);

@@ -111,6 +111,11 @@ struct StepArgs {
   // the same scalars rounded to FP32 for the FP32-arithmetic kernels (no
   // double-to-float conversions on the device)
   float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt, f_mu_exp;
+  // FP32 equilibrium velocity u^_a = j_a fl(1/c_s) / rho (1 + g_a): the
+  // rounding of the FP32 tables' first moment folded out (zero for FP64).
+  // f_g for the isothermal BGK form (1 - 1/tau) f + (w/tau) e, f_gc for the
+  // compressible form f - (f - w e) / tau.
+  float f_g[3], f_gc[3];
 };
 
 // Launch of the fused step for storage `storage` (olb_storage); returns a
@@ -144,7 +149,8 @@ struct StepInfo {
   int ctas_per_sm;
   size_t smem;
   int bxw, by, bz, tile, tx, ty, tz, vec;
-  int wg;  // warpgroups of the two-phase kernel (0: the single-role kernel runs)
+  int wg;    // warpgroups of the two-phase kernels (0: the single-role kernel runs)
+  int kmax;  // planes per warpgroup the kernel holds (0: no limit)
 };
 // Adjoint step of the isothermal two-phase kernel (FP64 and FP32 storage);
 // -1 when the configuration is not built.
@@ -153,6 +159,10 @@ int launch_adj_f64_3d(const StepLaunch& L);
 int launch_adj_f32_2d(const StepLaunch& L);
 int launch_adj_f32_3d(const StepLaunch& L);
 
+// mode: 0 the automatic choice (the two-phase kernel where it is built, else
+// the single-role kernel), 1 the single-role kernel, 2 the two-phase kernel
+// (the geometry of the adjoint), 3 the register-resident kernel where it is
+// built (else as 0).
 int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f64_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f32_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);

@@ -24,6 +24,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "olb_internal.h"
 
 namespace olb {
@@ -136,6 +138,32 @@ struct Layout {
   static_assert(TILE == NT * 4, "each thread owns one 4-node x group");
   static_assert(28 + 4 * ((VEC - 1 + 3 + P) / 4 + 1) <= BXW, "x pass reads inside the box row");
 };
+
+// ---------------------------------------------------------------------------
+// Velocity of the FP32 equilibrium.  With the abscissae and weights rounded to
+// FP32, the tables' first moment sum_i w_i xi_i (xi_i / c_s) differs from c_s I
+// by their rounding (1e-8 to 6e-8 relative).  An equilibrium built on
+// u^ = j / (rho c_s) would then carry the momentum j (1 + g) instead of j, and
+// the collision would scale the momentum by that factor at every step.  The
+// host computes the diagonal correction (the tables are symmetric under the
+// reflection of every axis, so the first moment is diagonal) and the velocity
+// is u^_a = j_a r (1 - g_a) with r = fl(1/c_s) / rho.  The correction is below
+// half an FP32 ulp, so it enters before the single rounding of an FMA: it then
+// acts on average instead of being rounded away.  FP64 runs use j r.
+// ---------------------------------------------------------------------------
+template <bool COMP, typename C>
+__device__ __forceinline__ C uhat_of(const StepArgs& a, C j, C r, int axis) {
+  if constexpr (std::is_same<C, float>::value) {
+    const float g = COMP ? a.f_gc[axis] : a.f_g[axis];
+    return fmaf(j, r, j * (r * g));
+  } else {
+    return j * r;
+  }
+}
+__device__ __forceinline__ float2 uhat2_of(const StepArgs& a, float2 j, float2 r, int axis) {
+  const float2 g = make_float2(a.f_g[axis], a.f_g[axis]);
+  return __ffma2_rn(j, r, __fmul2_rn(j, __fmul2_rn(r, g)));
+}
 
 // ---------------------------------------------------------------------------
 // mbarrier / TMA helpers (PTX)
@@ -472,7 +500,9 @@ __global__ void __launch_bounds__(NT, 1)
   using L = Layout<D, P, S>;
   using C = typename Store<S>::C;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
+  // 128-byte aligned base, kept as arithmetic on the shared array so that the
+  // compiler addresses it as shared memory (no generic loads and stores)
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   S* boxes[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + L::BOXB)};
   C* bufA = reinterpret_cast<C*>(base + L::OFF_A);
   C* bufB = reinterpret_cast<C*>(base + L::OFF_B);
@@ -617,10 +647,10 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       rho[e] = C(a.rho_ref) + Ad[e];
-      const C ir = C(1) / rho[e];
-      uhx[e] = jx[e] * ir * ics;
-      uhy[e] = jy[e] * ir * ics;
-      uhz[e] = jz[e] * ir * ics;
+      const C ir = ics / rho[e];
+      uhx[e] = uhat_of<COMP>(a, jx[e], ir, 0);
+      uhy[e] = uhat_of<COMP>(a, jy[e], ir, 1);
+      uhz[e] = uhat_of<COMP>(a, jz[e], ir, 2);
       q[e] = uhx[e] * uhx[e] + uhy[e] * uhy[e] + uhz[e] * uhz[e];
       if (COMP) {
         // temperature relation (Sec. 3) in FP64: energy minus kinetic part cancels
@@ -669,9 +699,15 @@ __global__ void __launch_bounds__(NT, 1)
         for (int e = 0; e < 4; ++e) {
           const C s = fma(xhx, uhx[e], fma(xhy, uhy[e], xhz * uhz[e]));
           const C ph = phi_m1<C, COMP>(s, q[e], tt[e], rD, rp, a.N);
-          const C feqd = wi * fma(rho[e], ph, Ad[e]);
+          const C eqv = fma(rho[e], ph, Ad[e]);  // A + rho Phi
+          const C feqd = wi * eqv;
           fneq[e] = v[b][e] - feqd;
-          o[e] = fma(-fneq[e], itau[e], v[b][e]);
+          // isothermal FP32: (1 - 1/tau) f + (w/tau)(A + rho Phi), the form whose
+          // first moment the host's correction f_g makes exact (see uhat_of)
+          if (!COMP && std::is_same<C, float>::value)
+            o[e] = fma(C(1) - C(a.f_inv_tau), v[b][e], C(vt.wt[i]) * eqv);
+          else
+            o[e] = fma(-fneq[e], itau[e], v[b][e]);
           if (COMP) {
             const C geqd = wi * C(a.gfac) * fma(rth[e], ph, gA[e]);
             og[e] = fma(-(vg[b][e] - geqd), itau[e], vg[b][e]);

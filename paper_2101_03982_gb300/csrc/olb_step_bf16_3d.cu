@@ -67,7 +67,7 @@ bool pick_wg(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {
 int launch_step_bf16_3d(const StepLaunch& L) {
   WgLaunch l;
   WgOcc o;
-  if (!L.force_generic && pick_wg(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);
+  if (L.force_generic != 1 && pick_wg(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);
   if (L.P == 2 && L.compressible == 0) return launch_one<3, 2, S, false>(L);
   if (L.P == 2 && L.compressible == 1) return launch_one<3, 2, S, true>(L);
   if (L.P == 3 && L.compressible == 0) return launch_one<3, 3, S, false>(L);
@@ -81,6 +81,7 @@ int step_info_bf16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo
   WgLaunch l;
   WgOcc o;
   out->wg = 0;
+  out->kmax = 0;
   if (P == 2) {
     layout_of<3, 2, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 2, S, true>(&out->smem)
@@ -89,7 +90,7 @@ int step_info_bf16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo
   }
   if (P == 3) {
     layout_of<3, 3, S>(out);
-    if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
+    if (force_generic != 1 && pick_wg(P, comp, Q, N, &l, &o)) {
       out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;
     }
@@ -99,7 +100,7 @@ int step_info_bf16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo
   }
   if (P == 4) {
     layout_of<3, 4, S>(out);
-    if (!force_generic && pick_wg(P, comp, Q, N, &l, &o)) {
+    if (force_generic != 1 && pick_wg(P, comp, Q, N, &l, &o)) {
       out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;
     }

@@ -312,6 +312,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   // phase B on node pairs with the paired FP32 pipe (isothermal, FP32 arithmetic, up to 27 velocities)
   constexpr bool PAIRS = !ADJ && !COMP && std::is_same<C, float>::value && QM <= 27;
   constexpr bool APAIRS = ADJ && std::is_same<C, float>::value && QM <= 27 && N <= 3;
+  // isothermal FP32 arithmetic relaxes as (1 - 1/tau) f + (w/tau)(A + rho Phi),
+  // the form whose first moment the host's correction f_g makes exact (see uhat_of)
+  constexpr bool ISO32 = !COMP && std::is_same<C, float>::value;
   // phase B from shared-memory chunks of the staging slab (see Staging)
   using SG = Staging<D, P, S, COMP, QM, ADJ>;
   constexpr int SPMAX = SG::SPMAX;
@@ -322,7 +325,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   using T2 = typename PR::T;
   constexpr int NT = L::NT;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
+  // 128-byte aligned base, kept as arithmetic on the shared array so that the
+  // compiler addresses it as shared memory (no generic loads and stores)
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wg = tid / WGT, wt = tid % WGT;
   unsigned char* mine = base + wg * L::WGB;
@@ -725,7 +730,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       const C rho = sc.rho_ref + A;
       const C ir = C(1) / rho;
-      const C uhx = jx * ir * sc.inv_cs, uhy = jy * ir * sc.inv_cs, uhz = jz * ir * sc.inv_cs;
+      const C irc = sc.inv_cs / rho;
+      const C uhx = uhat_of<COMP>(a, jx, irc, 0), uhy = uhat_of<COMP>(a, jy, irc, 1), uhz = uhat_of<COMP>(a, jz, irc, 2);
       const C q = uhx * uhx + uhy * uhy + uhz * uhz;
       C itau = sc.inv_tau, tt = C(0), gA = C(0), rth = C(0), theta = C(1), tau = sc.tau;
       if (COMP) {
@@ -802,10 +808,12 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
         const C ph = phi(i);
-        const C feqd = vt.w[i] * fma(rho, ph, A);
+        const C eqv = fma(rho, ph, A);  // A + rho Phi
+        const C feqd = vt.w[i] * eqv;
         const C fi = src[i * stride];
         const C fneq = fi - feqd;
-        im.put(pf, Store<S>::st(fma(-fneq, itau, fi)), pd, off, x, y, z);
+        im.put(pf, Store<S>::st(ISO32 ? fma(C(1) - sc.inv_tau, fi, vt.wt[i] * eqv) : fma(-fneq, itau, fi)), pd, off, x,
+               y, z);
         pf += pd.plane;
         if (R) {
 #pragma unroll
@@ -876,7 +884,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       const C rho = sc.rho_ref + A;
       const C ir = C(1) / rho;
-      const C uhx = jx * ir * sc.inv_cs, uhy = jy * ir * sc.inv_cs, uhz = jz * ir * sc.inv_cs;
+      const C irc = sc.inv_cs / rho;
+      const C uhx = uhat_of<COMP>(a, jx, irc, 0), uhy = uhat_of<COMP>(a, jy, irc, 1), uhz = uhat_of<COMP>(a, jz, irc, 2);
       const C q = uhx * uhx + uhy * uhy + uhz * uhz;
       C itau = sc.inv_tau, tt = C(0), gA = C(0), rth = C(0), theta = C(1), tau = sc.tau;
       if (COMP) {
@@ -953,9 +962,11 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
         const C ph = phi(i);
-        const C feqd = vt.w[i] * fma(rho, ph, A);
+        const C eqv = fma(rho, ph, A);  // A + rho Phi
+        const C feqd = vt.w[i] * eqv;
         const C fneq = f[i] - feqd;
-        im.put(pf, Store<S>::st(fma(-fneq, itau, f[i])), pd, off, x, y, z);
+        im.put(pf, Store<S>::st(ISO32 ? fma(C(1) - sc.inv_tau, f[i], vt.wt[i] * eqv) : fma(-fneq, itau, f[i])), pd, off,
+               x, y, z);
         pf += pd.plane;
         if (R) {
 #pragma unroll
@@ -1021,7 +1032,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       const float2 rho = add2(f2(sc.rho_ref), A);
       const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
-      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 uhx = uhat2_of(a, jx, irc, 0), uhy = uhat2_of(a, jy, irc, 1), uhz = uhat2_of(a, jz, irc, 2);
       const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
       const float2 r2 = mul2(f2(0.5f), rho);
       float2 c = fma2(f2(-1.f), mul2(r2, q), A);
@@ -1093,7 +1104,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       }
       const float2 rho = add2(f2(sc.rho_ref), A);
       const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
-      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 uhx = uhat2_of(a, jx, irc, 0), uhy = uhat2_of(a, jy, irc, 1), uhz = uhat2_of(a, jz, irc, 2);
       const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
       const float2 r2 = mul2(f2(0.5f), rho);
       float2 c = fma2(f2(-1.f), mul2(r2, q), A);
@@ -1202,7 +1213,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       for (int i = 0; i < QM; ++i) sig[i] = i < Q ? *reinterpret_cast<const float2*>(sg + (size_t)i * L::TILE) : f2(0.f);
       const float2 rho = add2(f2(sc.rho_ref), A);
       const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
-      const float2 uhx = mul2(jx, irc), uhy = mul2(jy, irc), uhz = mul2(jz, irc);
+      const float2 uhx = uhat2_of(a, jx, irc, 0), uhy = uhat2_of(a, jy, irc, 1), uhz = uhat2_of(a, jz, irc, 2);
       const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
       float2 ca = f2(0.f), bx = f2(0.f), by = f2(0.f), bz = f2(0.f), bq = f2(0.f);
 #pragma unroll
@@ -1279,8 +1290,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
       C sig[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) sig[i] = i < Q ? sg[(size_t)i * L::TILE] : C(0);
-      const C ir = C(1) / (sc.rho_ref + A);
-      const C uhx = jx * ir * sc.inv_cs, uhy = jy * ir * sc.inv_cs, uhz = jz * ir * sc.inv_cs;
+      const C irc = sc.inv_cs / (sc.rho_ref + A);
+      const C uhx = uhat_of<COMP>(a, jx, irc, 0), uhy = uhat_of<COMP>(a, jy, irc, 1), uhz = uhat_of<COMP>(a, jz, irc, 2);
       const C q = uhx * uhx + uhy * uhy + uhz * uhz;
       C ca = C(0), bx = C(0), by = C(0), bz = C(0), bq = C(0);
 #pragma unroll
