@@ -88,7 +88,7 @@ def algorithmic_flops(w):
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("olb_step.cuh", "olb_wg.cuh", "olb_rr.cuh", "olb_step_f32_3d.cu"):
+    for f in ("olb_step.cuh", "olb_wg.cuh", "olb_step_f32_3d.cu"):
         h.update(open(os.path.join(ROOT, "paper_2101_03982_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -213,7 +213,7 @@ def per_set_table(torch, flush):
     rows = []
     specs = []
     for vs in ("D3Q13", "D3Q21", "D3V27", "D3Q27"):
-        for st in ("fp32", "bf16", "fp64"):
+        for st in ("fp32", "bf16", "fp16", "fp64"):
             specs.append(dict(WORKLOAD, velocity_set=vs, storage=st))
     specs.append(dict(WORKLOAD, velocity_set="D3V27", N=3))
     specs.append(dict(WORKLOAD, kernel="generic"))
@@ -251,6 +251,42 @@ def per_set_table(torch, flush):
                             fp64_alu_frac=round(fl / fp64_peak, 4), flops_per_node=algorithmic_flops(w))
         sim.close()
         del sim
+        torch.cuda.empty_cache()
+    return rows
+
+
+def history_run(w, torch, steps, log):
+    """k and the dissipation estimate every `log` steps of one run of workload w."""
+    sim, _ = make_sim(dict(w, log_every=log), torch)
+    ks, es = [], []
+    for _ in range(steps // log):
+        sim.step(log)
+        k, e = sim.kinetic_energy()
+        ks.append(k)
+        es.append(e)
+    sim.close()
+    return np.array(ks), np.array(es)
+
+
+def precision_table(torch, steps):
+    """The weakly compressible Taylor-Green runs (Sec. 4.2) at 128^3 for
+    `steps` steps with k and the dissipation estimate every 10 steps, per set,
+    in every storage: the largest relative deviation of each history from the
+    FP64 storage run (whose step matches the FP64 oracle to 1e-12 per step)."""
+    rows = []
+    for vs in ("D3Q27", "D3Q13", "D3Q21", "D3V27"):
+        w = dict(WORKLOAD, velocity_set=vs)
+        t0 = time.perf_counter()
+        k64, e64 = history_run(dict(w, storage="fp64"), torch, steps, 10)
+        t64 = time.perf_counter() - t0
+        for st in ("fp32", "bf16", "fp16"):
+            k, e = history_run(dict(w, storage=st), torch, steps, 10)
+            rows.append(dict(velocity_set=vs, storage=st, grid=[w["n"]] * 3, steps=steps, log_every=10,
+                             k_err_vs_fp64=float((np.abs(k - k64) / np.abs(k64)).max()),
+                             eps_err_vs_fp64=float((np.abs(e - e64) / np.abs(e64)).max()),
+                             k_final=float(k[-1]), k_final_fp64=float(k64[-1])))
+        rows.append(dict(velocity_set=vs, storage="fp64", grid=[w["n"]] * 3, steps=steps, log_every=10,
+                         k_final=float(k64[-1]), seconds=round(t64, 2)))
         torch.cuda.empty_cache()
     return rows
 
@@ -485,6 +521,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-per-set", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=2000,
+                    help="steps of the FP32/BF16/FP16-vs-FP64 history comparison (0: skip)")
     ap.add_argument("--workload", default="d3q27", choices=sorted(WORKLOADS),
                     help="timed workload (the reported metric is quoted on the default)")
     args = ap.parse_args()
@@ -540,6 +578,14 @@ def main():
 
     e2e = e2e_measure(w, torch)
     per_set = [] if args.no_per_set else per_set_table(torch, flush)
+    precision = [] if args.no_per_set or args.precision_steps <= 0 else precision_table(torch, args.precision_steps)
+    # the histories' deviations beside the throughput of the same set and storage
+    for r in per_set:
+        for q in precision:
+            if (r.get("velocity_set"), r.get("storage"), r.get("compressible"), r.get("N"), r.get("grid")) == \
+                    (q["velocity_set"], q["storage"], False, 2, q["grid"]) and "k_err_vs_fp64" in q:
+                r["err_vs_fp64"] = {"k_history": q["k_err_vs_fp64"], "eps_history": q["eps_err_vs_fp64"],
+                                    "steps": q["steps"]}
     adjoint = [] if args.no_per_set else adjoint_table(torch)
     diagnostics = None if args.no_per_set else diagnostics_timing(torch)
     cpu = None
@@ -579,6 +625,7 @@ def main():
         "clocks": clk.summary(),
         "k_final": k,
         "per_set": per_set,
+        "precision": precision,
         "adjoint": adjoint,
         "diagnostics": diagnostics,
     }

@@ -95,8 +95,7 @@ typedef struct {
   int allow_inexact; /* 1: accept a quadrature degree below 2N */
   int log_every;     /* the global sums are accumulated on steps whose count is a multiple of this (>= 1) */
   int kernel;        /* 0: automatic (the fastest step kernel built for the configuration), 1: the
-                        single-role step kernel, 2: the two-phase kernel (staging slab), where built,
-                        3: the register-resident kernel (isothermal FP32 3D, Q <= 28), where built */
+                        single-role step kernel, 2: the two-phase kernel (staging slab), where built */
   void* stream;      /* cudaStream_t for every call of the handle; NULL = default stream */
 } olb_options;
 

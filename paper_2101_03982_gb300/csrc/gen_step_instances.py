@@ -8,14 +8,10 @@ agree:
   built for: N = 2, 3 isothermal, N = 4 compressible; the velocity loop is
   unrolled to QM >= Q (9, 27 or 45);
 * otherwise the single-role kernel (olb_step.cuh), built for p = 1..6 in FP64
-  and p = 2..4 in the shifted storages;
-* on request (kernel mode 3), for FP32 storage in 3D, the register-resident
-  kernel (olb_rr.cuh) for the isothermal sets of up to RR_QMAX velocities,
-  p = 3, 4 and N = 2, 3.
+  and p = 2..4 in the shifted storages.
 
 The force_generic argument of launch_step_* and step_info_* is the kernel
-mode: 0 automatic, 1 single-role, 2 two-phase (the adjoint's geometry),
-3 register-resident where built (else as 0).
+mode: 0 automatic, 1 single-role, 2 two-phase (the adjoint's geometry).
 
 FP64 and FP32 files also define launch_adj_<storage>_<D>d, the adjoint step
 of the isothermal kernel for p = 3, 4 and the (Q, N) pairs in ADJ_CASES.
@@ -33,10 +29,6 @@ WG_ISO_N = [2, 3]
 WG_COMP_N = 4
 ADJ_STORAGES = ("f64", "f32")
 ADJ_CASES = {2: [(9, 2), (27, 2), (27, 3)], 3: [(27, 2), (27, 3), (45, 2)]}
-RR_STORAGES = {"f32": ("3",)}
-RR_P = [3, 4]
-RR_N = [2, 3]
-RR_QMAX = 28
 
 
 def iso_qms(D):
@@ -70,8 +62,7 @@ def emit(st, D):
     fn = f"{st}_{D}d"
     L = []
     L.append(f"// Instantiations of the fused step, {S} storage, D = {D}; written by gen_step_instances.py.")
-    rr = st in RR_STORAGES and str(D) in RR_STORAGES[st]
-    L.append('#include "olb_rr.cuh"' if rr else '#include "olb_wg.cuh"')
+    L.append('#include "olb_wg.cuh"')
     L.append("")
     L.append("namespace olb {")
     L.append("")
@@ -92,27 +83,11 @@ def emit(st, D):
         L.append("  }")
     L.append("  return false;")
     L.append("}")
-    if rr:
-        L.append("")
-        L.append("// Register-resident instance for (P, comp, Q, N), or null.")
-        L.append("bool pick_rr(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {")
-        L.append(f"  if (comp != 0 || Q > {RR_QMAX}) return false;")
-        for P in RR_P:
-            for N in RR_N:
-                L.append(f"  if (P == {P} && N == {N}) {{")
-                L.append(f"    *l = rr::launch_rr<{P}, {N}>;")
-                L.append(f"    *o = rr::occupancy_rr<{P}, {N}>;")
-                L.append("    return true;")
-                L.append("  }")
-        L.append("  return false;")
-        L.append("}")
     L.append("}  // namespace")
     L.append("")
     L.append(f"int launch_step_{fn}(const StepLaunch& L) {{")
     L.append("  WgLaunch l;")
     L.append("  WgOcc o;")
-    if rr:
-        L.append("  if (L.force_generic == 3 && pick_rr(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);")
     L.append("  if (L.force_generic != 1 && pick_wg(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);")
     for P in GENERIC_P[st]:
         for comp in (0, 1):
@@ -125,15 +100,9 @@ def emit(st, D):
     L.append("  WgLaunch l;")
     L.append("  WgOcc o;")
     L.append("  out->wg = 0;")
-    L.append("  out->kmax = 0;")
     for P in GENERIC_P[st]:
         L.append(f"  if (P == {P}) {{")
         L.append(f"    layout_of<{D}, {P}, S>(out);")
-        if rr and P in RR_P:
-            L.append("    if (force_generic == 3 && pick_rr(P, comp, Q, N, &l, &o)) {")
-            L.append("      out->ctas_per_sm = o(out);  // the register-resident kernel's own tile and shape")
-            L.append("      return 0;")
-            L.append("    }")
         if P in WG_P:
             L.append("    if (force_generic != 1 && pick_wg(P, comp, Q, N, &l, &o)) {")
             L.append("      out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape")

@@ -350,9 +350,7 @@ void layout_padding(olb_ctx* h) {
 
 // Planes of each warpgroup of the two-phase kernel: longest processing time
 // first, with a plane's cost from the passes its stencil needs.
-// kmax > 0 caps the planes of a warpgroup (the register-resident kernel holds
-// at most kmax planes per warpgroup); the caller guarantees planes <= nwg kmax.
-static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSchedule* out, int kmax = 0) {
+static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSchedule* out) {
   WgSchedule& S = *out;
   std::memset(&S, 0, sizeof(S));
   if (nwg < 1) nwg = 1;
@@ -360,12 +358,9 @@ static void lpt_schedule(int nwg, std::vector<std::pair<double, int>> cost, WgSc
   double load[4] = {0, 0, 0, 0};
   std::vector<int> lists[4];
   for (const auto& cp : cost) {
-    int best = -1;
-    for (int w = 0; w < nwg; ++w) {
-      if (kmax > 0 && (int)lists[w].size() >= kmax) continue;
-      if (best < 0 || load[w] < load[best]) best = w;
-    }
-    if (best < 0) best = 0;
+    int best = 0;
+    for (int w = 1; w < nwg; ++w)
+      if (load[w] < load[best]) best = w;
     load[best] += cp.first;
     lists[best].push_back(cp.second);
   }
@@ -390,7 +385,7 @@ static double plane_cost(const olb_ctx* h, int i) {
 static void build_schedule(olb_ctx* h) {
   std::vector<std::pair<double, int>> cost;
   for (int p = 0; p < h->planes; ++p) cost.push_back({plane_cost(h, p % h->Q), p});
-  lpt_schedule(h->info.wg, cost, &h->sched, h->info.kmax);
+  lpt_schedule(h->info.wg, cost, &h->sched);
 }
 
 namespace {
@@ -824,8 +819,8 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   if (!(opt.cs_scale > 0.0) || !std::isfinite(opt.cs_scale)) return fail(OLB_EINVAL, "cs_scale must be positive");
   if (!(opt.rho0 > 0.0)) return fail(OLB_EINVAL, "rho0 must be positive");
   if (opt.log_every < 1) return fail(OLB_EINVAL, "log_every must be >= 1");
-  if (opt.kernel < 0 || opt.kernel > 3)
-    return fail(OLB_EINVAL, "kernel must be 0 (automatic), 1 (single-role), 2 (two-phase) or 3 (register-resident)");
+  if (opt.kernel < 0 || opt.kernel > 2)
+    return fail(OLB_EINVAL, "kernel must be 0 (automatic), 1 (single-role) or 2 (two-phase)");
 
   VelocitySet vs;
   if (olb::velocity_set(velocity_set, &vs) != 0) return fail(OLB_EINVAL, "unknown velocity set");
@@ -855,7 +850,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->comp = opt.compressible ? 1 : 0;
   h->allow_inexact = opt.allow_inexact;
   h->log_every = opt.log_every;
-  h->force_generic = opt.kernel;  // kernel mode: 0 automatic, 1 single-role, 2 two-phase, 3 register-resident
+  h->force_generic = opt.kernel;  // kernel mode: 0 automatic, 1 single-role, 2 two-phase
   h->tau = tau;
   h->dt = dt;
   h->gamma = opt.gamma;
@@ -955,8 +950,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
 
   const size_t cbytes = h->storage == OLB_FP64 ? 8 : 4;
   const size_t state_bytes = (size_t)h->planes * h->pad.plane * h->elem;
-  // the register-resident kernel (kmax > 0) stages nothing in global memory
-  const size_t scratch_bytes = h->info.kmax > 0 ? 256 : (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
+  const size_t scratch_bytes = (size_t)h->step_grid * h->planes * h->info.tile * cbytes;
   for (int k = 0; k < 2; ++k) {
     e = cudaMalloc(&h->buf[k], state_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[k], 0, state_bytes, h->stream);

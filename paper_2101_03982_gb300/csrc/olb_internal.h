@@ -149,8 +149,7 @@ struct StepInfo {
   int ctas_per_sm;
   size_t smem;
   int bxw, by, bz, tile, tx, ty, tz, vec;
-  int wg;    // warpgroups of the two-phase kernels (0: the single-role kernel runs)
-  int kmax;  // planes per warpgroup the kernel holds (0: no limit)
+  int wg;  // warpgroups of the two-phase kernel (0: the single-role kernel runs)
 };
 // Adjoint step of the isothermal two-phase kernel (FP64 and FP32 storage);
 // -1 when the configuration is not built.
@@ -161,8 +160,7 @@ int launch_adj_f32_3d(const StepLaunch& L);
 
 // mode: 0 the automatic choice (the two-phase kernel where it is built, else
 // the single-role kernel), 1 the single-role kernel, 2 the two-phase kernel
-// (the geometry of the adjoint), 3 the register-resident kernel where it is
-// built (else as 0).
+// (the geometry of the adjoint).
 int step_info_f64_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f64_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f32_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);

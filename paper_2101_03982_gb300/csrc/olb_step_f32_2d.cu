@@ -81,7 +81,6 @@ int step_info_f32_2d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   WgLaunch l;
   WgOcc o;
   out->wg = 0;
-  out->kmax = 0;
   if (P == 2) {
     layout_of<2, 2, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<2, 2, S, true>(&out->smem)

@@ -1,5 +1,5 @@
 // Instantiations of the fused step, float storage, D = 3; written by gen_step_instances.py.
-#include "olb_rr.cuh"
+#include "olb_wg.cuh"
 
 namespace olb {
 
@@ -62,38 +62,11 @@ bool pick_wg(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {
   }
   return false;
 }
-
-// Register-resident instance for (P, comp, Q, N), or null.
-bool pick_rr(int P, int comp, int Q, int N, WgLaunch* l, WgOcc* o) {
-  if (comp != 0 || Q > 28) return false;
-  if (P == 3 && N == 2) {
-    *l = rr::launch_rr<3, 2>;
-    *o = rr::occupancy_rr<3, 2>;
-    return true;
-  }
-  if (P == 3 && N == 3) {
-    *l = rr::launch_rr<3, 3>;
-    *o = rr::occupancy_rr<3, 3>;
-    return true;
-  }
-  if (P == 4 && N == 2) {
-    *l = rr::launch_rr<4, 2>;
-    *o = rr::occupancy_rr<4, 2>;
-    return true;
-  }
-  if (P == 4 && N == 3) {
-    *l = rr::launch_rr<4, 3>;
-    *o = rr::occupancy_rr<4, 3>;
-    return true;
-  }
-  return false;
-}
 }  // namespace
 
 int launch_step_f32_3d(const StepLaunch& L) {
   WgLaunch l;
   WgOcc o;
-  if (L.force_generic == 3 && pick_rr(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);
   if (L.force_generic != 1 && pick_wg(L.P, L.compressible, L.a.Q, L.a.N, &l, &o)) return l(L);
   if (L.P == 2 && L.compressible == 0) return launch_one<3, 2, S, false>(L);
   if (L.P == 2 && L.compressible == 1) return launch_one<3, 2, S, true>(L);
@@ -108,7 +81,6 @@ int step_info_f32_3d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   WgLaunch l;
   WgOcc o;
   out->wg = 0;
-  out->kmax = 0;
   if (P == 2) {
     layout_of<3, 2, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 2, S, true>(&out->smem)
@@ -117,10 +89,6 @@ int step_info_f32_3d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   }
   if (P == 3) {
     layout_of<3, 3, S>(out);
-    if (force_generic == 3 && pick_rr(P, comp, Q, N, &l, &o)) {
-      out->ctas_per_sm = o(out);  // the register-resident kernel's own tile and shape
-      return 0;
-    }
     if (force_generic != 1 && pick_wg(P, comp, Q, N, &l, &o)) {
       out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;
@@ -131,10 +99,6 @@ int step_info_f32_3d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   }
   if (P == 4) {
     layout_of<3, 4, S>(out);
-    if (force_generic == 3 && pick_rr(P, comp, Q, N, &l, &o)) {
-      out->ctas_per_sm = o(out);  // the register-resident kernel's own tile and shape
-      return 0;
-    }
     if (force_generic != 1 && pick_wg(P, comp, Q, N, &l, &o)) {
       out->ctas_per_sm = o(out);  // the two-phase kernel's own tile and shape
       return 0;

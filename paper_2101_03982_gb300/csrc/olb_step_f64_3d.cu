@@ -87,7 +87,6 @@ int step_info_f64_3d(int P, int comp, int Q, int N, int force_generic, StepInfo*
   WgLaunch l;
   WgOcc o;
   out->wg = 0;
-  out->kmax = 0;
   if (P == 1) {
     layout_of<3, 1, S>(out);
     out->ctas_per_sm = comp ? occupancy_one<3, 1, S, true>(&out->smem)

@@ -172,7 +172,7 @@ class Sim:
         o.rho0 = float(rho0)
         o.allow_inexact = int(bool(allow_inexact))
         o.log_every = int(log_every)
-        o.kernel = {"auto": 0, "generic": 1, "twophase": 2, "rr": 3}[kernel]
+        o.kernel = {"auto": 0, "generic": 1, "twophase": 2}[kernel]
         if stream is None:
             try:
                 import torch

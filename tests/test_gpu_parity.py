@@ -128,10 +128,11 @@ def test_one_step_parity_generic_kernel(olb, name, shape, N, p, storage, comp, c
     _one_step(olb, name, shape, N, p, storage, comp, courant, cs, "generic")
 
 
-# the register-resident kernel (isothermal FP32 3D, up to 28 velocities):
-# several tiles (32 x 8 x 4), ragged tails, a grid smaller than one tile, an
-# odd nx (node-by-node stores), p = 3 and 4, N = 2 and 3
-RR_CASES = [
+# isothermal FP32 3D: every set of up to 27 velocities, several tiles and
+# several tiles per CTA (the last case), ragged tails, a grid smaller than one
+# tile, an odd nx (node-by-node stores), p = 3 and 4, N = 2 and 3, a Courant
+# number above 1
+ISO32_CASES = [
     ("D3Q27", (40, 20, 18), 2, 4, "fp32", False, 0.4, 1.0),
     ("D3Q27", (37, 20, 18), 2, 4, "fp32", False, 0.4, 1.0),
     ("D3Q27", (33, 9, 10), 2, 3, "fp32", False, 0.4, 1.0),
@@ -139,22 +140,15 @@ RR_CASES = [
     ("D3Q13", (32, 24, 17), 2, 4, "fp32", False, 0.4, 1.0),
     ("D3Q21", (36, 17, 11), 2, 4, "fp32", False, 0.4, 1.0),
     ("D3V27", (34, 16, 9), 3, 4, "fp32", False, 0.4, 1.0),
-    ("D3Q27", (64, 16, 12), 3, 4, "fp32", False, 1.3, 1.0),
+    ("D3Q27", (64, 16, 12), 2, 4, "fp32", False, 1.3, 1.0),
+    ("D3Q27", (160, 96, 80), 2, 4, "fp32", False, 0.4, 1.0),
 ]
 
 
-@pytest.mark.parametrize("name,shape,N,p,storage,comp,courant,cs", RR_CASES)
-def test_one_step_parity_register_resident_kernel(olb, name, shape, N, p, storage, comp, courant, cs):
-    _one_step(olb, name, shape, N, p, storage, comp, courant, cs, "rr")
-
-
-def test_ten_steps_fp32_register_resident_kernel(olb):
-    sim, prm, state = make_pair(olb, "D3Q27", (64, 24, 20), N=2, p=4, storage="fp32", kernel="rr")
-    want, _ = oracle_steps(prm, state, steps=10)
-    sim.step(10)
-    got = sim.get_populations(np.zeros_like(state))
-    assert rel_err(got, want, prm.vs.w, "fp32") < 1e-4
-    sim.close()
+@pytest.mark.parametrize("kernel", ["auto", "twophase"])
+@pytest.mark.parametrize("name,shape,N,p,storage,comp,courant,cs", ISO32_CASES)
+def test_one_step_parity_fp32_iso(olb, name, shape, N, p, storage, comp, courant, cs, kernel):
+    _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel)
 
 
 MU_OF_THETA = [
