@@ -121,7 +121,8 @@ int olb_velocity_set_table(int velocity_set, double* xi, double* w);
  * the Lagrange weights W[k (p + 1) + m] of the cell that contains the
  * departure point.  first: p ints, W: p (p + 1) doubles, caller-owned.  No
  * GPU needed.  OLB_EINVAL for p outside 1..OLB_GLC_MAX_P, a non-finite shift
- * or a null output.  (The step kernels do not use this layout yet.) */
+ * or a null output.  olb_set_interpolation(h, 1) runs the step with these
+ * stencils. */
 #define OLB_GLC_MAX_P 8
 int olb_glc_stencil(int p, double shift, int* first, double* W);
 
@@ -247,6 +248,22 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device);
  * then check the device error flag of the step kernels (no counterpart in the paper).
  * OLB_ETIMEOUT when the bound ran out or a step gave up waiting for a staging copy. */
 int olb_synchronize(olb_handle h, int timeout_ms);
+
+/* Interpolation of the pull (Sec. 3, Eq. sl_streaming).  scheme 0 (the
+ * default): one equidistant Lagrange stencil of degree p per velocity and axis
+ * on the uniform grid (every node has the same offset).  scheme 1: the
+ * paper's own streaming, cell-wise Lagrange interpolation on Gauss-Lobatto-
+ * Chebyshev points: every axis of n nodes is read as n / p cells of width
+ * p dx, node c p + k at the GLC point k of cell c, and the departure point of
+ * a node is interpolated with the Lagrange basis of the cell that contains it
+ * (the stencils of olb_glc_stencil, per velocity, axis and residue k, with the
+ * shift xi_a dt / (p dx)).  The moments, equilibrium and BGK are unchanged; a
+ * step is then two launches (the pull into the second buffer, then the
+ * collision), and the global sums stay plain node means.  OLB_EINVAL for
+ * another scheme or an axis whose length is not a multiple of p;
+ * OLB_EUNSUPPORTED for 16-bit storage or the inflow/outflow x boundary.  While
+ * scheme 1 is set the adjoint calls return OLB_EUNSUPPORTED. */
+int olb_set_interpolation(olb_handle h, int scheme);
 
 /* Bound of the step kernels' waits for their staging copies, in polls of the
  * copy's barrier (no counterpart in the paper; a diagnostic of the error path).

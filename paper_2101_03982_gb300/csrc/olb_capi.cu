@@ -57,6 +57,10 @@ struct olb_ctx {
   long long step_count = 0;
   int partials_valid = 0;  // 1: the partials hold the sums of the current state's step
   int state_bad = 0;       // 1: a step gave up waiting for a staging copy; no valid state since
+  int glc = 0;             // 1: cell-wise Gauss-Lobatto-Chebyshev interpolation (olb_set_interpolation)
+  GlcArgs glc_args{};
+  void* glc_w = nullptr;                   // device weights of the GLC pull
+  std::vector<unsigned char> st_glc_id;    // identity stencil: the collision of pulled values
   int xbc = 0;             // 1: non-periodic x (inflow / zero-gradient outflow ghost columns)
   XInflow inflow{};
   void* xbc_vals = nullptr;  // inflow value per plane, storage form
@@ -314,6 +318,7 @@ void release(olb_ctx* h) {
   if (h->adj_scratch) cudaFree(h->adj_scratch);
   if (h->ens_u) cudaFree(h->ens_u);
   if (h->xbc_vals) cudaFree(h->xbc_vals);
+  if (h->glc_w) cudaFree(h->glc_w);
   if (h->ens_part) cudaFree(h->ens_part);
   delete h;
 }
@@ -598,6 +603,7 @@ void fill_adj_tabs(olb_ctx* h) {
 // Buffers, tables and schedules of the adjoint sweep (once per handle).
 int adj_prepare(olb_ctx* h) {
   if (h->xbc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for periodic grids only");
+  if (h->glc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the uniform-grid interpolation only");
   if (h->adj_ready) return OLB_OK;
   if (h->comp) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the isothermal step only");
   if (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED)
@@ -732,6 +738,31 @@ int tape_grow(olb_ctx* h, int nslots) {
     }
   }
   return OLB_OK;
+}
+
+}  // namespace
+
+namespace {
+// Identity stencil in the arithmetic type C: no axis active.
+template <typename C, int P1>
+void identity_stencil_p(olb_ctx* h, std::vector<unsigned char>& out) {
+  out.assign(sizeof(StencilTab<C, P1>), 0);
+  auto* t = reinterpret_cast<StencilTab<C, P1>*>(out.data());
+  for (int i = 0; i < h->Q; ++i) {
+    t->active[i] = 0;
+    for (int a = 0; a < 3; ++a) t->W[i][a][0] = (C)1;
+  }
+}
+template <typename C>
+void identity_stencil(olb_ctx* h, std::vector<unsigned char>& out) {
+  switch (h->p) {
+    case 1: identity_stencil_p<C, 2>(h, out); break;
+    case 2: identity_stencil_p<C, 3>(h, out); break;
+    case 3: identity_stencil_p<C, 4>(h, out); break;
+    case 4: identity_stencil_p<C, 5>(h, out); break;
+    case 5: identity_stencil_p<C, 6>(h, out); break;
+    default: identity_stencil_p<C, 7>(h, out); break;
+  }
 }
 
 }  // namespace
@@ -1081,10 +1112,24 @@ int olb_step(olb_handle h, int n) {
   int rc = set_device(h);
   if (rc) return rc;
   StepLaunch L = base_launch(h);
+  if (h->glc) L.stentab = h->st_glc_id.data();
   for (int s = 0; s < n; ++s) {
     const long long count = h->step_count + 1;
-    L.a.src = h->cur;
     L.a.reduce = (count % h->log_every) == 0;
+    if (h->glc) {
+      // cell-wise GLC pull into the other buffer, then the collision of those
+      // values (the step kernel with the identity stencil) back into this one
+      rc = launch_rc(launch_glc_pull(h->storage, h->glc_args, h->buf[h->cur], h->buf[h->cur ^ 1], h->stream),
+                     "GLC pull");
+      if (rc) return rc;
+      L.a.src = h->cur ^ 1;
+      rc = launch_rc(launch_step(h->storage, h->D, L), "sl_step (collision)");
+      if (rc) return rc;
+      h->step_count = count;
+      h->partials_valid = L.a.reduce;
+      continue;
+    }
+    L.a.src = h->cur;
     const int r = launch_step(h->storage, h->D, L);
     rc = launch_rc(r, "sl_step");
     if (rc) return rc;
@@ -1311,6 +1356,8 @@ int olb_set_state(olb_handle h, const void* buf, size_t bytes, int on_device) {
 }
 
 int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, double theta) {
+  if (h && h->glc && kind != 0)
+    return fail(OLB_EUNSUPPORTED, "the inflow/outflow x boundary is built for the uniform-grid interpolation only");
   if (!h) return fail(OLB_EINVAL, "null handle");
   if (kind != 0 && kind != 1) return fail(OLB_EINVAL, "x boundary kind must be 0 (periodic) or 1 (inflow/outflow)");
   if (kind == 1) {
@@ -1355,6 +1402,73 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
   return rc;
 }
 
+int olb_set_interpolation(olb_handle h, int scheme) {
+  if (!h) return fail(OLB_EINVAL, "null handle");
+  if (scheme != 0 && scheme != 1) return fail(OLB_EINVAL, "scheme must be 0 (uniform Lagrange) or 1 (cell-wise GLC)");
+  if (scheme == 0) {
+    h->glc = 0;
+    return OLB_OK;
+  }
+  if (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED)
+    return fail(OLB_EUNSUPPORTED, "the cell-wise GLC pull is built for FP64 and FP32 storage");
+  if (h->xbc) return fail(OLB_EUNSUPPORTED, "the cell-wise GLC pull is built for periodic grids only");
+  if (h->p > GLC_PMAX) return fail(OLB_EUNSUPPORTED, "GLC order above the built maximum");
+  for (int a = 0; a < h->D; ++a)
+    if (h->grid.n[a] % h->p != 0)
+      return fail(OLB_EINVAL, "every axis must hold a whole number of cells (n multiple of p)");
+  int rc = set_device(h);
+  if (rc) return rc;
+  GlcArgs& g = h->glc_args;
+  g = GlcArgs{};
+  g.pad = h->pad;
+  g.nnodes = h->nnodes;
+  g.planes = h->planes;
+  g.Q = h->Q;
+  g.D = h->D;
+  g.p = h->p;
+  const size_t nw = (size_t)MAXQ * 3 * GLC_PMAX * (GLC_PMAX + 1);
+  std::vector<double> wd(nw, 0.0);
+  const double H = h->p * h->grid.dx;  // cell width: p nodes per cell
+  for (int i = 0; i < h->Q; ++i) {
+    int act = 0;
+    for (int a = 0; a < h->D; ++a) {
+      if (h->set.xi[i][a] != 0.0) act |= 1 << a;
+      int first[GLC_PMAX];
+      double W[GLC_PMAX * (GLC_PMAX + 1)];
+      rc = olb_glc_stencil(h->p, h->set.xi[i][a] * h->dt / H, first, W);
+      if (rc) return rc;
+      for (int k = 0; k < h->p; ++k) {
+        const int idx = (i * 3 + a) * GLC_PMAX + k;
+        g.first[idx] = first[k];
+        for (int m = 0; m <= h->p; ++m) wd[(size_t)idx * (GLC_PMAX + 1) + m] = W[k * (h->p + 1) + m];
+      }
+    }
+    g.active[i] = act;
+  }
+  const bool f64 = h->storage == OLB_FP64;
+  const size_t bytes = nw * (f64 ? sizeof(double) : sizeof(float));
+  if (!h->glc_w) {
+    cudaError_t e = cudaMalloc(&h->glc_w, (size_t)nw * sizeof(double));
+    if (e != cudaSuccess) return fail(OLB_ENOMEM, std::string("GLC weights: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e;
+  if (f64) {
+    e = cudaMemcpyAsync(h->glc_w, wd.data(), bytes, cudaMemcpyHostToDevice, h->stream);
+  } else {
+    std::vector<float> wf(nw);
+    for (size_t k = 0; k < nw; ++k) wf[k] = (float)wd[k];
+    e = cudaMemcpyAsync(h->glc_w, wf.data(), bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "GLC weights upload");
+  g.W = h->glc_w;
+  if (f64) identity_stencil<double>(h, h->st_glc_id);
+  else identity_stencil<float>(h, h->st_glc_id);
+  h->glc = 1;
+  return OLB_OK;
+}
+
 int olb_set_wait_polls(olb_handle h, long long polls) {
   if (!h) return fail(OLB_EINVAL, "null handle");
   h->args.wait_polls = polls < 0 ? (1LL << 24) : polls;
@@ -1383,6 +1497,7 @@ int olb_tape_reserve(olb_handle h, int nslots) {
 int olb_tape_record(olb_handle h, int n) {
   if (!h) return fail(OLB_EINVAL, "null handle");
   if (h->xbc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for periodic grids only");
+  if (h->glc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the uniform-grid interpolation only");
   if (n < 0) return fail(OLB_EINVAL, "negative step count");
   if (n + 1 > (int)h->tape.size()) return fail(OLB_EBOUNDS, "tape has fewer than n + 1 slots");
   int rc = set_device(h);

@@ -170,6 +170,22 @@ int step_info_bf16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo
 int step_info_f16_2d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 int step_info_f16_3d(int P, int comp, int Q, int N, int force_generic, StepInfo* out);
 
+// Pull of the cell-wise interpolation on Gauss-Lobatto-Chebyshev points
+// (olb_glc.cu): per velocity i, axis a and residue k = node mod p, the first
+// support node relative to the node and the p + 1 Lagrange weights.
+constexpr int GLC_PMAX = 8;
+struct GlcArgs {
+  Padded pad;
+  long long nnodes;
+  int planes, Q, D, p;
+  int active[MAXQ];                 // bit a: xi_{i,a} != 0
+  int first[MAXQ * 3 * GLC_PMAX];   // [i][a][k]
+  const void* W;                    // device [i][a][k][GLC_PMAX + 1], arithmetic type of the storage
+};
+// storage 0 (FP64) or 1 (FP32); -1 for a storage not built.  Writes the pulled
+// values of every plane of src into the interior of dst (padded layouts).
+int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream);
+
 // Auxiliary kernels (olb_aux.cu).
 struct AuxArgs {
   Padded pad;

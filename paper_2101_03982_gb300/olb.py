@@ -68,6 +68,7 @@ def lib():
             "olb_set_state": (i, [vp, vp, sz, i]),
             "olb_synchronize": (i, [vp, i]),
             "olb_set_wait_polls": (i, [vp, ctypes.c_longlong]),
+            "olb_set_interpolation": (i, [vp, i]),
             "olb_state_sums_noalloc": (i, [i, ctypes.POINTER(Grid), i, d, d, vp, vp, vp]),
             "olb_enstrophy": (i, [vp, dp]),
             "olb_tape_reserve": (i, [vp, i]),
@@ -288,6 +289,10 @@ class Sim:
 
     def synchronize(self, timeout_ms=0):
         _check(lib().olb_synchronize(self._h, int(timeout_ms)))
+
+    def set_interpolation(self, scheme):
+        """"uniform" (equidistant Lagrange stencil) or "glc" (the paper's cell-wise GLC interpolation)."""
+        _check(lib().olb_set_interpolation(self._h, {"uniform": 0, "glc": 1}[scheme]))
 
     def set_wait_polls(self, polls):
         """Bound of the step kernels' staging waits (< 0: the default; 0: give up at once)."""
