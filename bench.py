@@ -45,6 +45,15 @@ WORKLOADS = {
     "d3q27-fp64": dict(WORKLOAD, storage="fp64"),
     "d2q19-comp": dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
                        Ma=1.2, Re=800.0, courant=0.4),
+    "d2q25-comp": dict(velocity_set="D2Q25", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
+                       Ma=1.2, Re=800.0, courant=0.4),
+    "d3q13": dict(WORKLOAD, velocity_set="D3Q13"),
+    "d3q21": dict(WORKLOAD, velocity_set="D3Q21"),
+    "d3v27": dict(WORKLOAD, velocity_set="D3V27"),
+    "d3q27-bf16": dict(WORKLOAD, storage="bf16"),
+    "d3q27-fp16": dict(WORKLOAD, storage="fp16"),
+    "d2q9-fp64": dict(velocity_set="D2Q9", n=64, N=2, p=3, storage="fp64", courant=0.4, Re=100.0, Ma=0.0866),
+    "d3q27-glc": dict(WORKLOAD, interp="glc"),
 }
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
@@ -59,9 +68,14 @@ def workload_name(w):
                 f"{w['shape'][1]}, inflow/outflow in x, periodic in y, {w['velocity_set']}, N={w['N']} Hermite "
                 f"equilibrium, f+g, gamma 1.4, "
                 f"p={w['p']} Lagrange pull, Courant {w['courant']}, {w['storage'].upper()} shifted storage")
+    if w["velocity_set"].startswith("D2"):  # the 2D Taylor-Green vortex
+        return (f"2D Taylor-Green vortex Re={w['Re']:g}, {w['n']}^2 periodic, {w['velocity_set']} (c_s^2 = 1/3), "
+                f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
+                f"{w['storage'].upper()} storage")
     kind = "compressible (f+g, gamma 1.4) " if w.get("compressible") else ""
     return (f"{kind}3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
-            f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
+            f"N={w['N']} Hermite equilibrium, p={w['p']} "
+            f"{'cell-wise GLC' if w.get('interp') == 'glc' else 'Lagrange'} pull, Courant {w['courant']}, "
             f"{w['storage'].upper()} {'shifted ' if w['storage'] != 'fp64' else ''}storage, "
             f"k and dissipation every {w.get('log_every', 1)} steps")
 
@@ -190,6 +204,8 @@ def make_sim(w, torch):
                   kernel=w.get("kernel", "auto"))
     rho, u = inputs.tgv3d(w["n"], rp.u0, rp.cs ** 2)
     sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    if w.get("interp") == "glc":  # the paper's cell-wise GLC pull (two launches per step)
+        sim.set_interpolation("glc")
     return sim, w["n"] ** 3
 
 
@@ -217,6 +233,8 @@ def per_set_table(torch, flush):
             specs.append(dict(WORKLOAD, velocity_set=vs, storage=st))
     specs.append(dict(WORKLOAD, velocity_set="D3V27", N=3))
     specs.append(dict(WORKLOAD, kernel="generic"))
+    specs.append(dict(WORKLOAD, interp="glc"))
+    specs.append(dict(WORKLOAD, interp="glc", storage="fp64"))
     specs.append(dict(WORKLOAD, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
@@ -241,7 +259,8 @@ def per_set_table(torch, flush):
         t = statistics.mean(ts)
         s = sim.elem_bytes
         nbytes = 2 * sim.planes * s * nodes
-        rows.append(dict(kernel=w.get("kernel", "auto"), velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
+        rows.append(dict(kernel=w.get("kernel", "auto"), interp=w.get("interp", "uniform"),
+                         velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
                          N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
                          mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
                          gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))
@@ -621,7 +640,8 @@ def main():
                      "kernel": "sl_wg_kernel (two-phase fused pull + collide), FP64"},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * (2 if "shape" in w else 1),  # the 2D shock adds its x-boundary fill
+        # the 2D shock adds its x-boundary fill, the cell-wise GLC step its pull kernel
+        "gpu_launches": args.steps * (2 if ("shape" in w or w.get("interp") == "glc") else 1),
         "clocks": clk.summary(),
         "k_final": k,
         "per_set": per_set,

@@ -47,4 +47,8 @@ def test_workload_names_state_the_grid(name):
     w = bench.WORKLOADS[name]
     text = bench.workload_name(w)
     assert w["velocity_set"] in text
-    assert (f"{w['n']}^3" in text) if "n" in w else (f"{w['shape'][0]}x{w['shape'][1]}" in text)
+    if "n" in w:
+        dim = 2 if w["velocity_set"].startswith("D2") else 3
+        assert f"{w['n']}^{dim}" in text
+    else:
+        assert f"{w['shape'][0]}x{w['shape'][1]}" in text
