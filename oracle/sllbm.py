@@ -23,6 +23,18 @@ and notation, with no blocking or fusion:
   mu(theta) = mu theta^omega (omega = mu_exponent, 0 by default) is a
   builder's extension, pinned by the decay of a shear wave at two
   temperatures (the model's kinematic viscosity is mu(theta)/rho).
+* Prandtl number (Sec. 3 states that a quasi-equilibrium varies Pr and
+  gives no formula): the reading here is the heat-flux quasi-equilibrium of
+  two-population kinetic models.  f* equals f^eq except that its central heat
+  flux sum_i f*_i zeta_i |zeta_i|^2 is that of the pulled f, and g* equals g^eq
+  except that its central first moment sum_i g*_i zeta_i is that of the pulled
+  g; the step relaxes to f* at tau and from f* to f^eq at
+  tau_2 = 1/2 + (tau - 1/2)/Pr, so the heat flux relaxes at tau_2 and every
+  other non-conserved moment at tau.  ``quasi_equilibrium`` builds f* and g*
+  as f^eq and g^eq plus the Hermite projections of the two non-equilibrium
+  fluxes (exact on sets of degree >= 7).  Pinned by the decay of an isobaric
+  temperature wave (thermal diffusivity nu/Pr) and by a shear wave that keeps
+  its viscosity at any Pr.
 
 Readings where the paper is silent (each listed in the design notes):
 T0 = c_s^2 of the set; C_v = 1/(gamma - 1); one step = pull, then collide, and
@@ -281,10 +293,13 @@ def temperature(vs, f, g, rho, u, gamma):
 class Params:
     """Run parameters of one simulation (grid units: dx, dt; tau or mu)."""
 
-    def __init__(self, vs, N, p, dt, dx, tau=None, compressible=False, gamma=1.4, mu=None, mu_exponent=0.0):
+    def __init__(self, vs, N, p, dt, dx, tau=None, compressible=False, gamma=1.4, mu=None, mu_exponent=0.0,
+                 prandtl=1.0):
         self.vs, self.N, self.p, self.dt, self.dx = vs, N, p, dt, dx
         self.tau, self.compressible, self.gamma, self.mu = tau, compressible, gamma, mu
-        self.mu_exponent = mu_exponent
+        self.mu_exponent, self.prandtl = mu_exponent, prandtl
+        if prandtl != 1.0 and not compressible:
+            raise ValueError("the Prandtl number is a parameter of the compressible model")
         if compressible and mu is None:
             raise ValueError("compressible runs need the dynamic viscosity mu")
         if not compressible and tau is None:
@@ -301,6 +316,31 @@ def pull_state(prm, f, inflow=None):
     if inflow is None:
         return np.stack([pull_plane(f[i], deltas[i], prm.p) for i in range(f.shape[0])])
     return np.stack([pull_plane_xbc(f[i], deltas[i % Q], prm.p, inflow[i]) for i in range(f.shape[0])])
+
+
+def quasi_equilibrium(vs, ft, gt, feq, geq, u):
+    """The quasi-equilibria f*, g* of the heat flux (Prandtl reading above).
+
+    With zeta_i = xi_i - u and T0 = c_s^2, the non-equilibrium central heat
+    flux of f, q_f = sum_i (f~_i - f^eq_i) zeta_i |zeta_i|^2, and the
+    non-equilibrium central first moment of g, q_g = sum_i (g~_i - g^eq_i) zeta_i,
+    are carried by the third- and first-order Hermite terms
+        f*_i - f^eq_i = w_i (q_f . xi_i)(|xi_i|^2 - (D + 2) T0) / (2 (D + 2) T0^3),
+        g*_i - g^eq_i = w_i (q_g . xi_i) / T0,
+    which have no mass, momentum, stress or energy, and whose central heat
+    flux (first moment for g) is q_f (q_g) when the set integrates sixth-order
+    monomials exactly.  All arrays (Q, M) except u (M, D)."""
+    D, T0 = vs.D, vs.cs ** 2
+    zeta = vs.xi[:, None, :] - u[None, :, :]
+    zeta2 = (zeta ** 2).sum(axis=2)
+    q_f = np.einsum("im,ima->ma", (ft - feq) * zeta2, zeta, optimize=False)
+    q_g = np.einsum("im,ima->ma", gt - geq, zeta, optimize=False)
+    xi2 = (vs.xi ** 2).sum(axis=1)
+    qf_xi = q_f @ vs.xi.T  # (M, Q)
+    qg_xi = q_g @ vs.xi.T
+    fstar = feq + (vs.w[:, None] * qf_xi.T * (xi2[:, None] - (D + 2) * T0)) / (2.0 * (D + 2) * T0 ** 3)
+    gstar = geq + vs.w[:, None] * qg_xi.T / T0
+    return fstar, gstar
 
 
 def collide(prm, ft, gt=None):
@@ -326,6 +366,13 @@ def collide(prm, ft, gt=None):
         Cv = 1.0 / (prm.gamma - 1.0)
         geq = theta[None, :] * (2.0 * Cv - vs.D) * feq
         gpost = gt - (gt - geq) / tau[None, :]
+        if prm.prandtl != 1.0:
+            # relax to f* at tau, and from f* to f^eq at tau_2 (heat flux)
+            tau2 = 0.5 + (tau - 0.5) / prm.prandtl
+            fstar, gstar = quasi_equilibrium(vs, ft, gt, feq, geq, u)
+            c = (1.0 / tau - 1.0 / tau2)[None, :]
+            fpost = fpost + c * (fstar - feq)
+            gpost = gpost + c * (gstar - geq)
     diag = dict(rho=rho, u=u, theta=theta, tau=tau, ft=ft, feq=feq)
     return fpost, gpost, diag
 
