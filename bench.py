@@ -41,12 +41,13 @@ WORKLOAD = dict(velocity_set="D3Q27", n=128, Re=1600.0, Ma=0.1, courant=0.4, N=2
 WORKLOADS = {
     "d3q27": WORKLOAD,
     "d3q45": dict(WORKLOAD, velocity_set="D3Q45"),
-    "d3q45-comp": dict(WORKLOAD, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0),
+    # compressible runs: Pr = 0.75 as in Secs. 4.1 and 4.3 (heat-flux quasi-equilibrium)
+    "d3q45-comp": dict(WORKLOAD, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0, prandtl=0.75),
     "d3q27-fp64": dict(WORKLOAD, storage="fp64"),
     "d2q19-comp": dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
-                       Ma=1.2, Re=800.0, courant=0.4),
+                       Ma=1.2, Re=800.0, courant=0.4, prandtl=0.75),
     "d2q25-comp": dict(velocity_set="D2Q25", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
-                       Ma=1.2, Re=800.0, courant=0.4),
+                       Ma=1.2, Re=800.0, courant=0.4, prandtl=0.75),
     "d3q13": dict(WORKLOAD, velocity_set="D3Q13"),
     "d3q21": dict(WORKLOAD, velocity_set="D3Q21"),
     "d3v27": dict(WORKLOAD, velocity_set="D3V27"),
@@ -66,13 +67,13 @@ def workload_name(w):
     if "shape" in w:  # the 2D shock-vortex field
         return (f"2D shock-vortex interaction (Mach {w['Ma']:g} standing shock, isentropic vortex), {w['shape'][0]}x"
                 f"{w['shape'][1]}, inflow/outflow in x, periodic in y, {w['velocity_set']}, N={w['N']} Hermite "
-                f"equilibrium, f+g, gamma 1.4, "
+                f"equilibrium, f+g, gamma 1.4, Pr {w.get('prandtl', 1.0):g}, "
                 f"p={w['p']} Lagrange pull, Courant {w['courant']}, {w['storage'].upper()} shifted storage")
     if w["velocity_set"].startswith("D2"):  # the 2D Taylor-Green vortex
         return (f"2D Taylor-Green vortex Re={w['Re']:g}, {w['n']}^2 periodic, {w['velocity_set']} (c_s^2 = 1/3), "
                 f"N={w['N']} Hermite equilibrium, p={w['p']} Lagrange pull, Courant {w['courant']}, "
                 f"{w['storage'].upper()} storage")
-    kind = "compressible (f+g, gamma 1.4) " if w.get("compressible") else ""
+    kind = f"compressible (f+g, gamma 1.4, Pr {w.get('prandtl', 1.0):g}) " if w.get("compressible") else ""
     return (f"{kind}3D Taylor-Green vortex Re={w['Re']:g} Ma={w['Ma']:g}, {w['n']}^3 periodic, {w['velocity_set']}, "
             f"N={w['N']} Hermite equilibrium, p={w['p']} "
             f"{'cell-wise GLC' if w.get('interp') == 'glc' else 'Lagrange'} pull, Courant {w['courant']}, "
@@ -177,7 +178,7 @@ def make_sim(w, torch):
             mu = math.sqrt(1.4) * w["Ma"] * (0.075 * ny) / w["Re"]
             sim = olb.Sim((nx, ny), 1.0, w["velocity_set"], w["N"], 1.0, dt, interp_order=w["p"],
                           storage=w["storage"], compressible=True, gamma=1.4, mu=mu,
-                          log_every=w.get("log_every", 10))
+                          log_every=w.get("log_every", 10), prandtl=w.get("prandtl", 1.0))
             rho, u, th = inputs.shock_vortex(nx, ny, Ma_a=w["Ma"])
             sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda(),
                             torch.from_numpy(th).cuda())
@@ -187,7 +188,7 @@ def make_sim(w, torch):
         rp = params.tgv_compressible(w["velocity_set"], w["n"], w["Re"], w["Ma"], w["courant"])
         sim = olb.Sim((w["n"],) * 3, rp.dx, w["velocity_set"], w["N"], rp.tau, rp.dt, interp_order=w["p"],
                       storage=w["storage"], compressible=True, gamma=rp.gamma, mu=rp.mu,
-                      log_every=w.get("log_every", 10))
+                      log_every=w.get("log_every", 10), prandtl=w.get("prandtl", 1.0))
         rho, u, th = inputs.ctic3d(w["n"], rp.u0)
         sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(th).cuda())
         return sim, w["n"] ** 3
@@ -238,12 +239,11 @@ def per_set_table(torch, flush):
     specs.append(dict(WORKLOAD, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
-    specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0))
-    specs.append(dict(WORKLOAD, n=512, velocity_set="D3Q45", N=4, compressible=True, Ma=1.0))  # 99 GB of A/B
-    specs.append(dict(velocity_set="D2Q19", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
-                      Ma=1.2, Re=800.0, courant=0.4))
-    specs.append(dict(velocity_set="D2Q25", shape=(1024, 512), N=4, p=4, storage="fp32", compressible=True,
-                      Ma=1.2, Re=800.0, courant=0.4))
+    specs.append(dict(WORKLOADS["d3q45-comp"], n=256))
+    specs.append(dict(WORKLOADS["d3q45-comp"], n=256, prandtl=1.0))  # plain BGK, the cost of the Pr model
+    specs.append(dict(WORKLOADS["d3q45-comp"], n=512))  # 99 GB of A/B
+    specs.append(WORKLOADS["d2q19-comp"])
+    specs.append(WORKLOADS["d2q25-comp"])
     specs.append(dict(velocity_set="D2Q9", n=64, N=2, p=3, storage="fp64", courant=0.4, Re=100.0, Ma=0.0866))
     hbm, _ = measured_peaks()
     from paper_2101_03982_gb300 import olb
@@ -262,6 +262,7 @@ def per_set_table(torch, flush):
         rows.append(dict(kernel=w.get("kernel", "auto"), interp=w.get("interp", "uniform"),
                          velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
                          N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
+                         prandtl=w.get("prandtl", 1.0),
                          mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
                          gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))
         if w["storage"] == "fp64":  # bound by the FP64 pipe: % of the measured FP64 FMA peak first
@@ -308,6 +309,25 @@ def precision_table(torch, steps):
                          k_final=float(k64[-1]), seconds=round(t64, 2)))
         torch.cuda.empty_cache()
     return rows
+
+
+def precision_comp_table(torch, n, steps):
+    """The compressible Taylor-Green run (Sec. 4.3: D3Q45, N = 4, Ma 1.0,
+    Pr 0.75) at n^3 for `steps` steps with k logged every 10 steps, FP32
+    shifted storage against FP64 storage: the largest relative deviation of
+    the k history."""
+    w = dict(WORKLOADS["d3q45-comp"], n=n)
+    t0 = time.perf_counter()
+    k64, e64 = history_run(dict(w, storage="fp64"), torch, steps, 10)
+    t64 = time.perf_counter() - t0
+    k32, e32 = history_run(dict(w, storage="fp32"), torch, steps, 10)
+    torch.cuda.empty_cache()
+    return [dict(velocity_set="D3Q45", compressible=True, Ma=w["Ma"], prandtl=w["prandtl"], storage="fp32",
+                 grid=[n] * 3, steps=steps, log_every=10,
+                 k_err_vs_fp64=float((np.abs(k32 - k64) / np.abs(k64)).max()),
+                 eps_err_vs_fp64=float((np.abs(e32 - e64) / np.abs(e64)).max()),
+                 k_final=float(k32[-1]), k_final_fp64=float(k64[-1]), k0_fp64=float(k64[0]),
+                 fp64_seconds=round(t64, 1))]
 
 
 def adjoint_table(torch):
@@ -542,6 +562,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision-steps", type=int, default=2000,
                     help="steps of the FP32/BF16/FP16-vs-FP64 history comparison (0: skip)")
+    ap.add_argument("--precision-comp-steps", type=int, default=0,
+                    help="steps of the compressible D3Q45 FP32-vs-FP64 k history (0: skip; minutes of FP64)")
+    ap.add_argument("--precision-comp-n", type=int, default=128, help="grid of that comparison")
     ap.add_argument("--workload", default="d3q27", choices=sorted(WORKLOADS),
                     help="timed workload (the reported metric is quoted on the default)")
     args = ap.parse_args()
@@ -598,6 +621,8 @@ def main():
     e2e = e2e_measure(w, torch)
     per_set = [] if args.no_per_set else per_set_table(torch, flush)
     precision = [] if args.no_per_set or args.precision_steps <= 0 else precision_table(torch, args.precision_steps)
+    if args.precision_comp_steps > 0:
+        precision += precision_comp_table(torch, args.precision_comp_n, args.precision_comp_steps)
     # the histories' deviations beside the throughput of the same set and storage
     for r in per_set:
         for q in precision:

@@ -91,6 +91,13 @@ typedef struct {
   double gamma;      /* heat capacity ratio (compressible), C_v = 1/(gamma-1) */
   double mu;         /* dynamic viscosity (compressible; the tau argument is then ignored) */
   double mu_exponent; /* compressible: mu(theta) = mu theta^mu_exponent (0: constant mu, as in Sec. 3) */
+  double prandtl;    /* compressible: Prandtl number (default 1, plain BGK).  Sec. 3 varies Pr with a
+                        quasi-equilibrium and gives no form; the form built here: f relaxes at tau to
+                        f*, the equilibrium carrying the pulled f's central heat flux
+                        sum_i f_i zeta_i |zeta_i|^2 (zeta = xi - u), and from f* to f^eq at
+                        tau_2 = 1/2 + (tau - 1/2)/Pr; g likewise with its central first moment.
+                        Pr != 1 needs N >= 3 and a set of degree >= 7 (OLB_EUNSUPPORTED otherwise) and
+                        is refused for isothermal runs (OLB_EINVAL). */
   double rho0;       /* reference density of the shifted storage (default 1) */
   int allow_inexact; /* 1: accept a quadrature degree below 2N */
   int log_every;     /* the global sums are accumulated on steps whose count is a multiple of this (>= 1) */
@@ -102,7 +109,8 @@ typedef struct {
 typedef struct olb_ctx* olb_handle;
 
 /* Fill *opt with defaults: p = 3, FP64, cs_scale = 1, isothermal, gamma = 1.4,
- * mu = 0, mu_exponent = 0, rho0 = 1, allow_inexact = 0, log_every = 1, kernel = 0, stream = NULL. */
+ * mu = 0, mu_exponent = 0, prandtl = 1, rho0 = 1, allow_inexact = 0, log_every = 1, kernel = 0,
+ * stream = NULL. */
 void olb_default_options(olb_options* opt);
 
 /* Abscissae count Q, dimension D, c_s, largest |xi_{i,alpha}| and degree of a

@@ -41,7 +41,8 @@ void olb::set_last_error(const std::string& msg) { g_last_error = msg; }
 struct olb_ctx {
   olb_grid grid{};
   int vs_id = 0, N = 2, p = 3, storage = 0, comp = 0, allow_inexact = 0;
-  double tau = 1.0, dt = 0.0, gamma = 1.4, mu = 0.0, mu_exp = 0.0, rho0 = 1.0, cs = 1.0, cs_scale = 1.0;
+  double tau = 1.0, dt = 0.0, gamma = 1.4, mu = 0.0, mu_exp = 0.0, prandtl = 1.0, rho0 = 1.0, cs = 1.0,
+         cs_scale = 1.0;
   VelocitySet set{};  // scaled abscissae
   int Q = 0, planes = 0, D = 0, elem = 8;
   long long nnodes = 0;
@@ -779,6 +780,7 @@ void olb_default_options(olb_options* opt) {
   opt->gamma = 1.4;
   opt->mu = 0.0;
   opt->mu_exponent = 0.0;
+  opt->prandtl = 1.0;
   opt->rho0 = 1.0;
   opt->allow_inexact = 0;
   opt->log_every = 1;
@@ -865,8 +867,15 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
     if (!(opt.gamma > 1.0)) return fail(OLB_EINVAL, "gamma must exceed 1");
     if (!(opt.mu > 0.0)) return fail(OLB_EINVAL, "compressible runs need mu > 0");
     if (!std::isfinite(opt.mu_exponent)) return fail(OLB_EINVAL, "mu_exponent must be finite");
+    if (!(opt.prandtl > 0.0) || !std::isfinite(opt.prandtl)) return fail(OLB_EINVAL, "prandtl must be positive");
+    // the heat-flux projection is exact only where the set integrates sixth
+    // moments, and f^eq has no central heat flux only for N >= 3
+    if (opt.prandtl != 1.0 && (vs.degree < 7 || hermite_order < 3))
+      return fail(OLB_EUNSUPPORTED, "prandtl != 1 needs N >= 3 and a velocity set of degree >= 7");
   } else if (!(tau > 0.5) || !std::isfinite(tau)) {
     return fail(OLB_EINVAL, "tau must exceed 1/2");
+  } else if (opt.prandtl != 1.0) {
+    return fail(OLB_EINVAL, "the Prandtl number is a parameter of the compressible model");
   }
   const long long nnodes = (long long)grid->n[0] * grid->n[1] * grid->n[2];
   if (nnodes > (1LL << 31) - 1) return fail(OLB_EBOUNDS, "grid larger than 2^31 nodes");
@@ -887,6 +896,7 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   h->gamma = opt.gamma;
   h->mu = opt.mu;
   h->mu_exp = opt.compressible ? opt.mu_exponent : 0.0;
+  h->prandtl = opt.compressible ? opt.prandtl : 1.0;
   h->rho0 = opt.rho0;
   h->cs_scale = opt.cs_scale;
   h->cs = cs;
@@ -966,6 +976,9 @@ int olb_create(const olb_grid* grid, int velocity_set, int hermite_order, double
   a.f_cs2 = (float)a.cs2;
   a.f_dt = (float)a.dt;
   a.f_mu_exp = (float)a.mu_exp;
+  a.qe = h->prandtl != 1.0 ? 1 : 0;
+  a.inv_pr = 1.0 / h->prandtl;
+  a.f_inv_pr = (float)a.inv_pr;
 
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -1429,23 +1442,42 @@ int olb_set_interpolation(olb_handle h, int scheme) {
   const size_t nw = (size_t)MAXQ * 3 * GLC_PMAX * (GLC_PMAX + 1);
   std::vector<double> wd(nw, 0.0);
   const double H = h->p * h->grid.dx;  // cell width: p nodes per cell
+  const bool f64 = h->storage == OLB_FP64;
+  int T[3];
+  glc_tile_shape(h->D, f64 ? 8 : 4, &T[0], &T[1], &T[2]);
+  g.ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    g.nt[a] = (h->grid.n[a] + T[a] - 1) / T[a];
+    g.ntiles *= g.nt[a];
+  }
+  g.box_elems = 0;
   for (int i = 0; i < h->Q; ++i) {
-    int act = 0;
+    int act = 0, ext[3] = {T[0], T[1], T[2]};
     for (int a = 0; a < h->D; ++a) {
-      if (h->set.xi[i][a] != 0.0) act |= 1 << a;
+      if (h->set.xi[i][a] == 0.0) continue;  // an axis the velocity does not move along: no pass
+      act |= 1 << a;
       int first[GLC_PMAX];
       double W[GLC_PMAX * (GLC_PMAX + 1)];
       rc = olb_glc_stencil(h->p, h->set.xi[i][a] * h->dt / H, first, W);
       if (rc) return rc;
+      int lo = 0, hi = 0;
       for (int k = 0; k < h->p; ++k) {
         const int idx = (i * 3 + a) * GLC_PMAX + k;
         g.first[idx] = first[k];
         for (int m = 0; m <= h->p; ++m) wd[(size_t)idx * (GLC_PMAX + 1) + m] = W[k * (h->p + 1) + m];
+        lo = std::max(lo, -first[k]);
+        hi = std::max(hi, first[k] + h->p);
       }
+      if (lo > 255 || hi > 255) return fail(OLB_EUNSUPPORTED, "GLC departure points too far for the staged box");
+      g.lo[i * 3 + a] = (unsigned char)lo;
+      g.hi[i * 3 + a] = (unsigned char)hi;
+      ext[a] += lo + hi;
     }
     g.active[i] = act;
+    g.box_elems = std::max(g.box_elems, ext[0] * ext[1] * ext[2]);
   }
-  const bool f64 = h->storage == OLB_FP64;
+  if (glc_smem_bytes(g, f64 ? 8 : 4) > 227 * 1024)
+    return fail(OLB_EUNSUPPORTED, "GLC departure points too far for the staged box (Courant number too large)");
   const size_t bytes = nw * (f64 ? sizeof(double) : sizeof(float));
   if (!h->glc_w) {
     cudaError_t e = cudaMalloc(&h->glc_w, (size_t)nw * sizeof(double));

@@ -7,13 +7,22 @@
 // every node), and is interpolated with that cell's Lagrange basis on its
 // p + 1 GLC points.  The host builds, per velocity, axis and residue, the
 // first support node (relative to the node) and the p + 1 weights
-// (olb_glc_stencil); this kernel applies their tensor product to every node of
-// every plane and writes the pulled values into the interior of a second
-// padded state, which the fused step kernel then collides with an identity
-// stencil.  Periodic wrap by index arithmetic (the ghost layers are not read).
+// (olb_glc_stencil), and per velocity and axis the reach of those stencils.
+//
+// One CTA pulls one tile of one population plane.  It loads the tile and its
+// reach into shared memory (rows along x, periodic wrap by index arithmetic:
+// the ghost layers are not read), then applies the tensor product as
+// separable passes, x, then y, then z, each reading the per-residue stencil
+// of its output coordinate; an axis along which the velocity does not move is
+// skipped.  The last pass writes the pulled values, coalesced along x, into
+// the interior of a second padded state, which the fused step kernel then
+// collides with an identity stencil.  The order of the passes is the nesting
+// of the tensor-product sum sum_z w_z sum_y w_y sum_x w_x f.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "olb_internal.h"
 #include "olb_step.cuh"
@@ -22,82 +31,163 @@ namespace olb {
 
 namespace {
 
+constexpr int GT = 256;  // threads per CTA (8 warps)
+constexpr int GTX = 32;  // tile width along x: one output per lane
+
+template <typename C>
+struct GlcTile {
+  static constexpr int TY = 8;
+  static constexpr int TZ = sizeof(C) == 8 ? 4 : 8;  // 3D; 2D tiles are GTX x 32
+};
+
+// one element copied global -> shared without passing through registers
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(unsigned dst, const void* src) {
+  if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
+}
+
 template <typename S, int D>
-__global__ void __launch_bounds__(256) glc_pull_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                       const GlcArgs a) {
+__global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                     const GlcArgs a) {
   using C = typename Store<S>::C;
-  const C* __restrict__ W = static_cast<const C*>(a.W);
-  const long long total = (long long)a.planes * a.nnodes;
+  constexpr int TY = D == 3 ? GlcTile<C>::TY : 32;
+  constexpr int TZ = D == 3 ? GlcTile<C>::TZ : 1;
+  constexpr int WS = GLC_PMAX + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* wsm = reinterpret_cast<C*>(smem_raw);  // [3][GLC_PMAX][WS] weights of this velocity
+  C* b0 = wsm + 3 * GLC_PMAX * WS;
+  C* b1 = b0 + a.box_elems;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = (int)(blockIdx.x % (unsigned)a.ntiles);
+  const int plane = (int)(blockIdx.x / (unsigned)a.ntiles);
+  const int i = plane % a.Q;
   const int p = a.p, p1 = a.p + 1;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int plane = (int)(t / a.nnodes);
-    const long long node = t - (long long)plane * a.nnodes;
-    const int i = plane % a.Q;
-    const int x = (int)(node % a.pad.n[0]);
-    const long long r = node / a.pad.n[0];
-    const int y = (int)(r % a.pad.n[1]), z = D == 3 ? (int)(r / a.pad.n[1]) : 0;
-    const int c[3] = {x, y, z};
-    // per axis: first support node (absolute, before the wrap), weights, count
-    int f0[3], cnt[3];
-    const C* w[3];
-    for (int ax = 0; ax < 3; ++ax) {
-      if (ax >= D || !((a.active[i] >> ax) & 1)) {
-        f0[ax] = c[ax];
-        cnt[ax] = 1;
-        w[ax] = nullptr;  // identity
-        continue;
-      }
-      const int k = c[ax] % p;
-      const int idx = (i * 3 + ax) * GLC_PMAX + k;
-      f0[ax] = c[ax] + a.first[idx];
-      cnt[ax] = p1;
-      w[ax] = W + (size_t)idx * (GLC_PMAX + 1);
+  const int tx = tile % a.nt[0], tr = tile / a.nt[0];
+  const int x0 = tx * GTX, y0 = (tr % a.nt[1]) * TY, z0 = (tr / a.nt[1]) * TZ;
+  const int act = a.active[i];
+  const int lox = a.lo[i * 3 + 0], loy = a.lo[i * 3 + 1], loz = D == 3 ? a.lo[i * 3 + 2] : 0;
+  const int ex = GTX + lox + a.hi[i * 3 + 0];
+  const int ey = TY + loy + a.hi[i * 3 + 1];
+  const int ez = D == 3 ? TZ + loz + a.hi[i * 3 + 2] : 1;
+  const int n0 = a.pad.n[0], n1 = a.pad.n[1], n2 = a.pad.n[2];
+
+  const C* __restrict__ W = static_cast<const C*>(a.W);
+  for (int t = threadIdx.x; t < 3 * p * p1; t += GT) {
+    const int ax = t / (p * p1), r = t - ax * (p * p1), k = r / p1, m = r - k * p1;
+    wsm[(ax * GLC_PMAX + k) * WS + m] = W[((size_t)(i * 3 + ax) * GLC_PMAX + k) * WS + m];
+  }
+
+  // the tile and its reach, rows along x: asynchronous element copies (no
+  // register round trip, so every copy of the CTA is in flight at once)
+  static_assert(std::is_same<S, C>::value, "the GLC pull stages the storage type as is");
+  const S* __restrict__ sp = src + (size_t)plane * a.pad.plane;
+  const unsigned b0s = smem_u32(b0);
+  for (int r = warp; r < ey * ez; r += GT / 32) {
+    const int yb = r % ey, zb = r / ey;
+    const S* __restrict__ row = sp + pad_index(a.pad, 0, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0);
+    for (int xb = lane; xb < ex; xb += 32)
+      cp_async_elem<sizeof(S)>(b0s + (unsigned)((r * ex + xb) * sizeof(S)), row + wrap(x0 - lox + xb, n0));
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+
+  C* cur = b0;
+  C* nxt = b1;
+  int cx = ex, cy = ey;
+  if (act & 1) {  // x pass: (ex, ey, ez) -> (GTX, ey, ez)
+    const int k = (x0 + lane) % p;
+    const int f = a.first[(i * 3 + 0) * GLC_PMAX + k] + lox + lane;
+    const C* w = wsm + (0 * GLC_PMAX + k) * WS;
+    for (int r = warp; r < ey * ez; r += GT / 32) {
+      const C* s = cur + r * cx + f;
+      C acc = C(0);
+      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m], acc);
+      nxt[r * GTX + lane] = acc;
     }
-    const S* sp = src + (size_t)plane * a.pad.plane;
-    C acc = C(0);
-    for (int mz = 0; mz < cnt[2]; ++mz) {
-      int zz = f0[2] + mz;
-      zz = ((zz % a.pad.n[2]) + a.pad.n[2]) % a.pad.n[2];
-      const C wz = w[2] ? w[2][mz] : C(1);
-      C accy = C(0);
-      for (int my = 0; my < cnt[1]; ++my) {
-        int yy = f0[1] + my;
-        yy = ((yy % a.pad.n[1]) + a.pad.n[1]) % a.pad.n[1];
-        const C wy = w[1] ? w[1][my] : C(1);
-        C accx = C(0);
-        for (int mx = 0; mx < cnt[0]; ++mx) {
-          int xx = f0[0] + mx;
-          xx = ((xx % a.pad.n[0]) + a.pad.n[0]) % a.pad.n[0];
-          const C wx = w[0] ? w[0][mx] : C(1);
-          accx = fma(wx, Store<S>::ld(sp[pad_index(a.pad, xx, yy, zz)]), accx);
-        }
-        accy = fma(wy, accx, accy);
-      }
-      acc = fma(wz, accy, acc);
+    C* t = cur;
+    cur = nxt;
+    nxt = t;
+    cx = GTX;
+    __syncthreads();
+  }
+  if (act & 2) {  // y pass: (GTX, ey, ez) -> (GTX, TY, ez)
+    for (int r = warp; r < TY * ez; r += GT / 32) {
+      const int oy = r % TY, oz = r / TY;
+      const int k = (y0 + oy) % p;
+      const int f = a.first[(i * 3 + 1) * GLC_PMAX + k] + loy + oy;
+      const C* w = wsm + (1 * GLC_PMAX + k) * WS;
+      const C* s = cur + (oz * cy + f) * GTX + lane;
+      C acc = C(0);
+      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m * GTX], acc);
+      nxt[(oz * TY + oy) * GTX + lane] = acc;
     }
-    dst[(size_t)plane * a.pad.plane + pad_index(a.pad, x, y, z)] = Store<S>::st(acc);
+    C* t = cur;
+    cur = nxt;
+    nxt = t;
+    cy = TY;
+    __syncthreads();
+  }
+  (void)cx;
+  // z pass (or the plain copy of the passes' result) into the padded interior
+  S* __restrict__ dp = dst + (size_t)plane * a.pad.plane;
+  const int gx = x0 + lane;
+  const bool zpass = D == 3 && (act & 4);
+  for (int r = warp; r < TY * TZ; r += GT / 32) {
+    const int oy = r % TY, oz = r / TY;
+    const int gy = y0 + oy, gz = z0 + oz;
+    C v;
+    if (zpass) {
+      const int k = gz % p;
+      const int f = a.first[(i * 3 + 2) * GLC_PMAX + k] + loz + oz;
+      const C* w = wsm + (2 * GLC_PMAX + k) * WS;
+      const C* s = cur + (f * cy + oy) * GTX + lane;
+      C acc = C(0);
+      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m * cy * GTX], acc);
+      v = acc;
+    } else {
+      v = cur[(oz * cy + oy) * GTX + lane];
+    }
+    if (gx < n0 && gy < n1 && gz < n2) dp[pad_index(a.pad, gx, gy, gz)] = Store<S>::st(v);
   }
 }
 
 template <typename S>
 int launch_typed(const GlcArgs& a, const void* src, void* dst, void* stream) {
-  const long long total = (long long)a.planes * a.nnodes;
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long blocks = (total + 255) / 256;
-  if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-  if (blocks < 1) blocks = 1;
+  using C = typename Store<S>::C;
+  const size_t bytes = glc_smem_bytes(a, sizeof(C));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (a.D == 2)
-    glc_pull_kernel<S, 2><<<(int)blocks, 256, 0, s>>>(static_cast<const S*>(src), static_cast<S*>(dst), a);
-  else
-    glc_pull_kernel<S, 3><<<(int)blocks, 256, 0, s>>>(static_cast<const S*>(src), static_cast<S*>(dst), a);
+  const unsigned blocks = (unsigned)a.planes * (unsigned)a.ntiles;
+  auto k2 = glc_pull_kernel<S, 2>;
+  auto k3 = glc_pull_kernel<S, 3>;
+  auto kern = a.D == 2 ? k2 : k3;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return (int)e;
+  kern<<<blocks, GT, bytes, s>>>(static_cast<const S*>(src), static_cast<S*>(dst), a);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
+
+void glc_tile_shape(int D, int elem, int* tx, int* ty, int* tz) {
+  *tx = GTX;
+  const bool f64 = elem == 8;
+  *ty = D == 3 ? (f64 ? GlcTile<double>::TY : GlcTile<float>::TY) : 32;
+  *tz = D == 3 ? (f64 ? GlcTile<double>::TZ : GlcTile<float>::TZ) : 1;
+}
+
+size_t glc_smem_bytes(const GlcArgs& a, int elem) {
+  return ((size_t)3 * GLC_PMAX * (GLC_PMAX + 1) + 2 * (size_t)a.box_elems) * (size_t)elem;
+}
 
 int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream) {
   switch (storage) {

@@ -103,6 +103,8 @@ struct StepArgs {
   double tau;           // isothermal tau
   double mu_dt;         // compressible: mu / (c_s^2 dt)
   double mu_exp;        // compressible: mu(theta) = mu theta^mu_exp
+  int qe;               // compressible, Pr != 1: heat-flux quasi-equilibrium
+  double inv_pr;        // 1 / Pr
   double two_cv;        // 2 C_v
   double gfac;          // 2 C_v - D
   double inv_cs;        // 1 / c_s
@@ -110,7 +112,7 @@ struct StepArgs {
   double dt;
   // the same scalars rounded to FP32 for the FP32-arithmetic kernels (no
   // double-to-float conversions on the device)
-  float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt, f_mu_exp;
+  float f_rho_ref, f_inv_tau, f_tau, f_mu_dt, f_two_cv, f_gfac, f_inv_cs, f_cs2, f_dt, f_mu_exp, f_inv_pr;
   // FP32 equilibrium velocity u^_a = j_a fl(1/c_s) / rho (1 + g_a): the
   // rounding of the FP32 tables' first moment folded out (zero for FP64).
   // f_g for the isothermal BGK form (1 - 1/tau) f + (w/tau) e, f_gc for the
@@ -178,10 +180,17 @@ struct GlcArgs {
   Padded pad;
   long long nnodes;
   int planes, Q, D, p;
+  int nt[3], ntiles;                // tiles per axis (glc_tile_shape) and their product
+  int box_elems;                    // largest staged box (tile plus reach) over the velocities
   int active[MAXQ];                 // bit a: xi_{i,a} != 0
   int first[MAXQ * 3 * GLC_PMAX];   // [i][a][k]
+  unsigned char lo[MAXQ * 3], hi[MAXQ * 3];  // [i][a] reach below and above the tile (0 when inactive)
   const void* W;                    // device [i][a][k][GLC_PMAX + 1], arithmetic type of the storage
 };
+// Tile of the GLC pull for dimension D and element size elem (8: FP64 arithmetic).
+void glc_tile_shape(int D, int elem, int* tx, int* ty, int* tz);
+// Dynamic shared memory of one CTA of the GLC pull (weights and two boxes).
+size_t glc_smem_bytes(const GlcArgs& a, int elem);
 // storage 0 (FP64) or 1 (FP32); -1 for a storage not built.  Writes the pulled
 // values of every plane of src into the interior of dst (padded layouts).
 int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream);

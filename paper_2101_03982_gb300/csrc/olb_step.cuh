@@ -676,6 +676,60 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < 6; ++c) Pi[e][c] = C(0);
     }
 
+    // Pr != 1: the heat-flux quasi-equilibrium (Sec. 3 compressible model).
+    // The pulled f's central heat flux H = sum_i f_i zeta^_i |zeta^_i|^2 and
+    // g's central first moment Gh = sum_i g_i zeta^_i (zeta^ = xi^ - u^, the
+    // equilibria contribute none: N >= 3, degree >= 7), with the shifted
+    // storage's w rho0 parts added in closed form (sum_i w_i zeta^_i
+    // |zeta^_i|^2 = -u^ (D + 2 + |u^|^2), sum_i w_i zeta^_i = -u^).  The
+    // collision then adds (1/tau - 1/tau_2) times their Hermite projections,
+    //   w_i (H . xi^_i)(|xi^_i|^2 - D - 2) / (2 (D + 2))  and  w_i (Gh . xi^_i).
+    C Fk[4][3], Gk[4][3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Fk[e][c] = Gk[e][c] = C(0);
+    const bool qe = COMP && a.qe != 0;
+    if (qe) {
+      C H[4][3], Gh[4][3], Gs[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        Gs[e] = C(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) H[e][c] = Gh[e][c] = C(0);
+      }
+      for (int i = 0; i < Q; ++i) {
+        C v[4], vg[4];
+        gld4(scr + (size_t)i * L::TILE, v, keep);
+        gld4(scr + (size_t)(Q + i) * L::TILE, vg, keep);
+        const C xhx = vt.xih[i][0], xhy = vt.xih[i][1], xhz = D == 3 ? vt.xih[i][2] : C(0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const C zx = xhx - uhx[e], zy = xhy - uhy[e], zz = xhz - uhz[e];
+          const C fz = v[e] * fma(zx, zx, fma(zy, zy, zz * zz));
+          H[e][0] = fma(fz, zx, H[e][0]);
+          H[e][1] = fma(fz, zy, H[e][1]);
+          H[e][2] = fma(fz, zz, H[e][2]);
+          Gh[e][0] = fma(vg[e], xhx, Gh[e][0]);
+          Gh[e][1] = fma(vg[e], xhy, Gh[e][1]);
+          Gh[e][2] = fma(vg[e], xhz, Gh[e][2]);
+          Gs[e] += vg[e];
+        }
+      }
+      const C rr = C(a.rho_ref), ipr = std::is_same<C, float>::value ? C(a.f_inv_pr) : C(a.inv_pr);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const C kap = itau[e] - C(1) / fma(rtau[e] - C(0.5), ipr, C(0.5));  // 1/tau - 1/tau_2
+        const C hr = rr * (C(D + 2) + q[e]), gr = fma(C(a.gfac), rr, Gs[e]);
+        const C uh[3] = {uhx[e], uhy[e], uhz[e]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Fk[e][c] = kap * C(0.5 / (D + 2)) * fma(-hr, uh[c], H[e][c]);
+          Gk[e][c] = kap * fma(-gr, uh[c], Gh[e][c]);
+        }
+      }
+    }
+
     const bool red = a.reduce != 0;
     // velocities in batches: the staging loads of a batch are all in flight
     // before the first one is used
@@ -711,6 +765,10 @@ __global__ void __launch_bounds__(NT, 1)
           if (COMP) {
             const C geqd = wi * C(a.gfac) * fma(rth[e], ph, gA[e]);
             og[e] = fma(-(vg[b][e] - geqd), itau[e], vg[b][e]);
+            if (qe) {
+              o[e] = fma(wi * (rD - C(2)), fma(Fk[e][0], xhx, fma(Fk[e][1], xhy, Fk[e][2] * xhz)), o[e]);
+              og[e] = fma(wi, fma(Gk[e][0], xhx, fma(Gk[e][1], xhy, Gk[e][2] * xhz)), og[e]);
+            }
           }
         }
         S* pf = dst + (long long)i * pd.plane;

@@ -64,7 +64,13 @@ struct GLayout {
   // and y passes write in place (each column belongs to one thread), the copy
   // of the next plane but one lands while a plane is processed
   static constexpr bool INPL = D == 3 && sizeof(S) == sizeof(C);
-  static constexpr size_t WGB = INPL ? 2 * BOXB : BOXB + ABYTES + BBYTES;  // shared memory of one warpgroup
+  // 3D with 16-bit storage: two boxes of the storage type and one work buffer
+  // of the arithmetic type; the first pass converts the box into the work
+  // buffer (the later passes run in place there), so the box takes the copy
+  // of the plane after next as soon as that pass is done
+  static constexpr bool TWO16 = D == 3 && sizeof(S) == 2;
+  static constexpr bool TWOBOX = INPL || TWO16;
+  static constexpr size_t WGB = INPL ? 2 * BOXB : TWO16 ? 2 * BOXB + ABYTES : BOXB + ABYTES + BBYTES;
   static constexpr size_t BUDGET = 227 * 1024 - 2048;
   // warpgroups per CTA (at most NWG_MAX); CTAS resident CTAs per SM share the 16 warps
   static constexpr int NWG_MAX = 4;
@@ -110,18 +116,75 @@ template <typename C>
 struct Scal;
 template <>
 struct Scal<float> {
-  float rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp;
+  float rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp, inv_pr;
   __device__ __forceinline__ explicit Scal(const StepArgs& a)
       : rho_ref(a.f_rho_ref), inv_tau(a.f_inv_tau), tau(a.f_tau), mu_dt(a.f_mu_dt), two_cv(a.f_two_cv),
-        gfac(a.f_gfac), inv_cs(a.f_inv_cs), cs2(a.f_cs2), dt(a.f_dt), mu_exp(a.f_mu_exp) {}
+        gfac(a.f_gfac), inv_cs(a.f_inv_cs), cs2(a.f_cs2), dt(a.f_dt), mu_exp(a.f_mu_exp), inv_pr(a.f_inv_pr) {}
 };
 template <>
 struct Scal<double> {
-  double rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp;
+  double rho_ref, inv_tau, tau, mu_dt, two_cv, gfac, inv_cs, cs2, dt, mu_exp, inv_pr;
   __device__ __forceinline__ explicit Scal(const StepArgs& a)
       : rho_ref(a.rho_ref), inv_tau(a.inv_tau), tau(a.tau), mu_dt(a.mu_dt), two_cv(a.two_cv), gfac(a.gfac),
-        inv_cs(a.inv_cs), cs2(a.cs2), dt(a.dt), mu_exp(a.mu_exp) {}
+        inv_cs(a.inv_cs), cs2(a.cs2), dt(a.dt), mu_exp(a.mu_exp), inv_pr(a.inv_pr) {}
 };
+
+// Pr != 1, the heat-flux quasi-equilibrium of the compressible model (Sec. 3
+// varies Pr by a quasi-equilibrium): from the pulled values of one node,
+// f_i = ldf(i) and g_i = ldg(i) (shifted storage: minus w_i rho0 and
+// w_i (2 C_v - D) rho0), the central heat flux H = sum_i f_i zeta^_i
+// |zeta^_i|^2 and g's central first moment Gh = sum_i g_i zeta^_i, zeta^ =
+// xi^ - u^ (the equilibria carry none for N >= 3 on sets of degree >= 7; the
+// shifts add -rho0 u^ (D + 2 + |u^|^2) and -(2 C_v - D) rho0 u^).  Returns
+// Fk = kap H / (2 (D + 2)) and Gk = kap Gh, kap = 1/tau - 1/tau_2,
+// tau_2 = 1/2 + (tau - 1/2)/Pr: the collision adds w_i (|xi^_i|^2 - D - 2)
+// (Fk . xi^_i) to f_i and w_i (Gk . xi^_i) to g_i.
+template <int D, typename C>
+__device__ __forceinline__ C qe_dot(const VelTab<C>& vt, int i, const C k[3]) {
+  C s = k[0] * vt.xih[i][0];
+  s = fma(k[1], vt.xih[i][1], s);
+  if (D == 3) s = fma(k[2], vt.xih[i][2], s);
+  return s;
+}
+
+// FULL: unroll the velocity loop completely (ldf reads a register array).
+template <int D, int QM, bool FULL, typename C, typename LF, typename LG>
+__device__ __forceinline__ void qe_coeffs(const VelTab<C>& vt, int Q, const Scal<C>& sc, LF ldf, LG ldg, C uhx,
+                                          C uhy, C uhz, C q, C itau, C tau, C Fk[3], C Gk[3]) {
+  C H[3] = {C(0), C(0), C(0)}, Gh[3] = {C(0), C(0), C(0)}, Gs = C(0);
+  auto add = [&](int i) {
+    const C fi = ldf(i), gi = ldg(i);
+    const C xhx = vt.xih[i][0], xhy = vt.xih[i][1], xhz = D == 3 ? vt.xih[i][2] : C(0);
+    const C zx = xhx - uhx, zy = xhy - uhy, zz = xhz - uhz;
+    const C fz = fi * fma(zx, zx, fma(zy, zy, zz * zz));
+    H[0] = fma(fz, zx, H[0]);
+    H[1] = fma(fz, zy, H[1]);
+    H[2] = fma(fz, zz, H[2]);
+    Gh[0] = fma(gi, xhx, Gh[0]);
+    Gh[1] = fma(gi, xhy, Gh[1]);
+    Gh[2] = fma(gi, xhz, Gh[2]);
+    Gs += gi;
+  };
+  if constexpr (FULL) {
+#pragma unroll
+    for (int i = 0; i < QM; ++i)
+      if (i < Q) add(i);
+  } else {
+#pragma unroll 3
+    for (int i = 0; i < QM; ++i) {
+      if (i >= Q) break;
+      add(i);
+    }
+  }
+  const C kap = itau - C(1) / fma(tau - C(0.5), sc.inv_pr, C(0.5));
+  const C hr = sc.rho_ref * (C(D + 2) + q), gr = fma(sc.gfac, sc.rho_ref, Gs);
+  const C uh[3] = {uhx, uhy, uhz};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Fk[c] = kap * C(0.5 / (D + 2)) * fma(-hr, uh[c], H[c]);
+    Gk[c] = kap * fma(-gr, uh[c], Gh[c]);
+  }
+}
 
 // Two values of the arithmetic type; FP32 pairs use the paired FMA.
 template <typename C>
@@ -187,8 +250,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 
 // x pass of one 4-node group from a row of C values (s: first node's column,
 // rounded down to the 16-byte granule; XO: offset of the first needed value).
-template <int P, int XO, bool XACT, typename C>
-__device__ __forceinline__ void xrow(const C* s, const C* W, C out[4]) {
+template <int P, int XO, bool XACT, typename SRC, typename C>
+__device__ __forceinline__ void xrow(const SRC* s, const C* W, C out[4]) {
   if (!XACT) {
     ld4(s, out);
     return;
@@ -205,6 +268,9 @@ __device__ __forceinline__ void xrow(const C* s, const C* W, C out[4]) {
     out[e] = acc;
   }
 }
+
+// 16-bit two-box staging: the x pass is the only pass of a plane at rest along y and z
+__device__ __forceinline__ bool from_box_plane(bool zact, bool yact) { return !zact && !yact; }
 
 __device__ __forceinline__ void wg_barrier(int wg) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(1 + wg), "r"(WGT) : "memory");
@@ -332,8 +398,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   const int wg = tid / WGT, wt = tid % WGT;
   unsigned char* mine = base + wg * L::WGB;
   S* box = reinterpret_cast<S*>(mine);
-  S* box1 = reinterpret_cast<S*>(mine + (L::INPL ? L::BOXB : 0));
-  C* bufA = reinterpret_cast<C*>(mine + L::BOXB);
+  S* box1 = reinterpret_cast<S*>(mine + (L::TWOBOX ? L::BOXB : 0));
+  C* bufA = reinterpret_cast<C*>(mine + (L::TWO16 ? 2 * L::BOXB : L::BOXB));
   C* bufB = reinterpret_cast<C*>(mine + L::BOXB + L::ABYTES);
   double* red_smem = reinterpret_cast<double*>(base + L::OFF_R);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(base + L::OFF_M) + 2 * wg;
@@ -411,10 +477,10 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   if (nplan > 0 && (int)blockIdx.x < a.ntiles) {
     if (wt == 0) {
       issue(blockIdx.x, sched.plane[wg][0]);
-      if (!L::INPL && nplan > 1) prefetch(blockIdx.x, sched.plane[wg][1]);
+      if (!L::TWOBOX && nplan > 1) prefetch(blockIdx.x, sched.plane[wg][1]);
     }
     pending = true;
-    if (L::INPL) {
+    if (L::TWOBOX) {
       int t1 = blockIdx.x, k1 = 0;
       advance(t1, k1, 1);
       if (t1 < a.ntiles) {
@@ -434,7 +500,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     // ---------------- phase A: pull every plane of the tile -----------------
-    if constexpr (L::INPL) {
+    if constexpr (L::TWOBOX) {
       for (int k = 0; k < nplan && !failed; ++k) {
         const int plane = sched.plane[wg][k];
         if (wg_any(wg, !mbar_wait_bounded(bar + cb, (parity >> cb) & 1u, a.wait_polls))) {
@@ -448,9 +514,25 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const auto& T = tab_of(plane);
         const int act = T.active[i];
         const bool zact = (act & 4) != 0, yact = (act & 2) != 0, xact = (act & 1) != 0;
-        C* bx = reinterpret_cast<C*>(cb ? box1 : box);
+        // bs: the staged plane; bx: where the passes run (the box itself when
+        // the storage is the arithmetic type, else the work buffer)
+        S* bs = cb ? box1 : box;
+        C* bx = L::INPL ? reinterpret_cast<C*>(bs) : bufA;
         const int BYA = yact ? L::BY : L::TY;
         const int PLs = BYA * L::BXW;
+        // 16-bit storage: the box is free once the first pass has read it
+        auto release = [&]() {
+          if constexpr (L::TWO16) {
+            wg_barrier(wg);
+            int t2 = tile, k2 = k;
+            advance(t2, k2, 2);
+            if (t2 < a.ntiles) {
+              if (wt == 0) issue(t2, sched.plane[wg][k2], cb);
+              if (cb) pending1 = true;
+              else pending = true;
+            }
+          }
+        };
         if (zact) {
           T2 W[P + 1];
 #pragma unroll
@@ -458,13 +540,14 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
           const int ncol = L::NQX * BYA;
           for (int col = wt; col < ncol; col += WGT) {
             const int q = col % L::NQX, y = col / L::NQX;
+            const S* s0 = bs + y * L::BXW + 4 * q;
             C* c0 = bx + y * L::BXW + 4 * q;
             T2 win[P + 1][2];
 #pragma unroll
-            for (int kk = 0; kk < P; ++kk) ld4p(c0 + kk * PLs, win[kk][0], win[kk][1]);
+            for (int kk = 0; kk < P; ++kk) ld4p(s0 + kk * PLs, win[kk][0], win[kk][1]);
 #pragma unroll
             for (int z = 0; z < L::TZ; ++z) {
-              ld4p(c0 + (z + P) * PLs, win[(z + P) % (P + 1)][0], win[(z + P) % (P + 1)][1]);
+              ld4p(s0 + (z + P) * PLs, win[(z + P) % (P + 1)][0], win[(z + P) % (P + 1)][1]);
               T2 o[2];
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
@@ -476,22 +559,26 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
               st4p(c0 + z * PLs, o[0], o[1]);  // row z is no longer read by this column
             }
           }
-          wg_barrier(wg);
+          if constexpr (L::TWO16) release();
+          else wg_barrier(wg);
         }
         if (yact) {
           T2 W[P + 1];
 #pragma unroll
           for (int j = 0; j <= P; ++j) W[j] = PR::set(T.W[i][1][j]);
           constexpr int ncol = L::NQX * L::TZ;
-          for (int col = wt; col < ncol; col += WGT) {
-            const int q = col % L::NQX, z = col / L::NQX;
-            C* c0 = bx + z * PLs + 4 * q;
-            T2 win[P + 1][2];
+          // in place in bx, or (16-bit storage, z at rest) from the box into bx
+          auto ypass_from = [&](const auto* src) {
+            for (int col = wt; col < ncol; col += WGT) {
+              const int q = col % L::NQX, z = col / L::NQX;
+              const auto* s0 = src + z * PLs + 4 * q;
+              C* c0 = bx + z * PLs + 4 * q;
+              T2 win[P + 1][2];
 #pragma unroll
-            for (int kk = 0; kk < P; ++kk) ld4p(c0 + kk * L::BXW, win[kk][0], win[kk][1]);
+              for (int kk = 0; kk < P; ++kk) ld4p(s0 + kk * L::BXW, win[kk][0], win[kk][1]);
 #pragma unroll
-            for (int y = 0; y < L::TY; ++y) {
-              ld4p(c0 + (y + P) * L::BXW, win[(y + P) % (P + 1)][0], win[(y + P) % (P + 1)][1]);
+              for (int y = 0; y < L::TY; ++y) {
+                ld4p(s0 + (y + P) * L::BXW, win[(y + P) % (P + 1)][0], win[(y + P) % (P + 1)][1]);
               T2 o[2];
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
@@ -500,16 +587,25 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
                 for (int kk = 1; kk <= P; ++kk) acc = PR::fma(W[kk], win[(y + kk) % (P + 1)][h], acc);
                 o[h] = acc;
               }
-              st4p(c0 + y * L::BXW, o[0], o[1]);
+                st4p(c0 + y * L::BXW, o[0], o[1]);
+              }
             }
+          };
+          if (L::TWO16 && !zact) {
+            ypass_from(static_cast<const S*>(bs));
+            release();
+          } else {
+            ypass_from(static_cast<const C*>(bx));
+            wg_barrier(wg);
           }
-          wg_barrier(wg);
         }
         {
           C W[P + 1];
 #pragma unroll
           for (int j = 0; j <= P; ++j) W[j] = T.W[i][0][j];
           const int xo = xact ? ((T.m0[i][0] % L::VEC) + L::VEC) % L::VEC : 0;
+          // the x pass reads bx, or (16-bit storage, y and z at rest) the box
+          const bool from_box = L::TWO16 && !zact && !yact;
           // one alignment variant per plane (dispatched once), rolled over the groups
           auto groups = [&](auto XOc, auto ACT) {
             constexpr int QPT = L::TILE / 4 / WGT;  // 4-node x groups per thread
@@ -520,7 +616,11 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
               const int qx = (qi % (L::TX / 4)) * 4, ly = (qi / (L::TX / 4)) % L::TY,
                         lz = qi / (L::TX / 4 * L::TY);
               C out[4];
-              xrow<P, decltype(XOc)::value, decltype(ACT)::value>(bx + (lz * BYA + ly) * L::BXW + qx, W, out);
+              const int off = (lz * BYA + ly) * L::BXW + qx;
+              if (from_box)
+                xrow<P, decltype(XOc)::value, decltype(ACT)::value>(bs + off, W, out);
+              else
+                xrow<P, decltype(XOc)::value, decltype(ACT)::value>(bx + off, W, out);
               gst4(so + 4 * qi, out, keep);
             }
           };
@@ -531,19 +631,29 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
               case 0: groups(std::integral_constant<int, 0>(), std::true_type()); break;
               case 1: groups(std::integral_constant<int, 1>(), std::true_type()); break;
               case 2: if constexpr (L::VEC > 2) groups(std::integral_constant<int, 2>(), std::true_type()); break;
-              default: if constexpr (L::VEC > 3) groups(std::integral_constant<int, 3>(), std::true_type()); break;
+              case 3: if constexpr (L::VEC > 3) groups(std::integral_constant<int, 3>(), std::true_type()); break;
+              case 4: if constexpr (L::VEC > 4) groups(std::integral_constant<int, 4>(), std::true_type()); break;
+              case 5: if constexpr (L::VEC > 5) groups(std::integral_constant<int, 5>(), std::true_type()); break;
+              case 6: if constexpr (L::VEC > 6) groups(std::integral_constant<int, 6>(), std::true_type()); break;
+              default: if constexpr (L::VEC > 7) groups(std::integral_constant<int, 7>(), std::true_type()); break;
             }
           }
         }
-        wg_barrier(wg);  // box free
-        int t2 = tile, k2 = k;
-        advance(t2, k2, 2);
-        // with shared-memory staging the boxes serve phase B: the next tile's
-        // copies start after it
-        if (t2 < a.ntiles && (!SMB || t2 == tile)) {
-          if (wt == 0) issue(t2, sched.plane[wg][k2], cb);
-          if (cb) pending1 = true;
-          else pending = true;
+        if (L::TWO16 && from_box_plane(zact, yact)) {
+          release();  // the x pass was the first to read the box; the work buffer was not used
+        } else {
+          wg_barrier(wg);  // box (work buffer) free
+          if constexpr (!L::TWO16) {
+            int t2 = tile, k2 = k;
+            advance(t2, k2, 2);
+            // with shared-memory staging the boxes serve phase B: the next tile's
+            // copies start after it
+            if (t2 < a.ntiles && (!SMB || t2 == tile)) {
+              if (wt == 0) issue(t2, sched.plane[wg][k2], cb);
+              if (cb) pending1 = true;
+              else pending = true;
+            }
+          }
         }
         cb ^= 1;
       }
@@ -758,6 +868,11 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         gA = fma(rho, tt, A);
         rth = rho * theta;
       }
+      C Fk[3], Gk[3];
+      const bool qe = COMP && a.qe != 0;
+      if (qe)
+        qe_coeffs<D, QM, false>(vt, Q, sc, [&](int i) { return src[i * stride]; },
+                         [&](int i) { return src[(Q + i) * stride]; }, uhx, uhy, uhz, q, itau, tau, Fk, Gk);
       const Images im = images_of(x, y, z);
       const long long off = pad_index(pd, x, y, z);
       // The closed form of order N (Appendix A) as a polynomial in s = xi^.u^,
@@ -812,8 +927,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const C feqd = vt.w[i] * eqv;
         const C fi = src[i * stride];
         const C fneq = fi - feqd;
-        im.put(pf, Store<S>::st(ISO32 ? fma(C(1) - sc.inv_tau, fi, vt.wt[i] * eqv) : fma(-fneq, itau, fi)), pd, off, x,
-               y, z);
+        C o = ISO32 ? fma(C(1) - sc.inv_tau, fi, vt.wt[i] * eqv) : fma(-fneq, itau, fi);
+        if (qe) o = fma(vt.w[i] * (vt.rD[i] - C(2)), qe_dot<D>(vt, i, Fk), o);
+        im.put(pf, Store<S>::st(o), pd, off, x, y, z);
         pf += pd.plane;
         if (R) {
 #pragma unroll
@@ -827,7 +943,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
           if (i >= Q) break;
           const C geqd = vt.w[i] * sc.gfac * fma(rth, phi(i), gA);
           const C gi = src[(Q + i) * stride];
-          im.put(pf, Store<S>::st(fma(-(gi - geqd), itau, gi)), pd, off, x, y, z);
+          C o = fma(-(gi - geqd), itau, gi);
+          if (qe) o = fma(vt.w[i], qe_dot<D>(vt, i, Gk), o);
+          im.put(pf, Store<S>::st(o), pd, off, x, y, z);
           pf += pd.plane;
         }
       }
@@ -912,6 +1030,12 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         gA = fma(rho, tt, A);
         rth = rho * theta;
       }
+      C Fk[3], Gk[3];
+      const bool qe = COMP && a.qe != 0;
+      if (qe)
+        qe_coeffs<D, QM, true>(vt, Q, sc, [&](int i) { return f[i]; },
+                         [&](int i) { return scr[(size_t)(Q + i) * L::TILE + n]; }, uhx, uhy, uhz, q, itau, tau, Fk,
+                         Gk);
       const Images im = images_of(x, y, z);
       const long long off = pad_index(pd, x, y, z);
       // The closed form of order N (Appendix A) as a polynomial in s = xi^.u^,
@@ -965,8 +1089,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         const C eqv = fma(rho, ph, A);  // A + rho Phi
         const C feqd = vt.w[i] * eqv;
         const C fneq = f[i] - feqd;
-        im.put(pf, Store<S>::st(ISO32 ? fma(C(1) - sc.inv_tau, f[i], vt.wt[i] * eqv) : fma(-fneq, itau, f[i])), pd, off,
-               x, y, z);
+        C o = ISO32 ? fma(C(1) - sc.inv_tau, f[i], vt.wt[i] * eqv) : fma(-fneq, itau, f[i]);
+        if (qe) o = fma(vt.w[i] * (vt.rD[i] - C(2)), qe_dot<D>(vt, i, Fk), o);
+        im.put(pf, Store<S>::st(o), pd, off, x, y, z);
         pf += pd.plane;
         if (R) {
 #pragma unroll
@@ -982,7 +1107,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         for (int i = 0; i < QM; ++i) {
           if (i >= Q) break;
           const C geqd = vt.w[i] * sc.gfac * fma(rth, phi(i), gA);
-          im.put(pf, Store<S>::st(fma(-(f[i] - geqd), itau, f[i])), pd, off, x, y, z);
+          C o = fma(-(f[i] - geqd), itau, f[i]);
+          if (qe) o = fma(vt.w[i], qe_dot<D>(vt, i, Gk), o);
+          im.put(pf, Store<S>::st(o), pd, off, x, y, z);
           pf += pd.plane;
         }
       }

@@ -32,7 +32,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("interp_order", ctypes.c_int), ("storage", ctypes.c_int), ("cs_scale", ctypes.c_double),
                 ("compressible", ctypes.c_int), ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
-                ("mu_exponent", ctypes.c_double), ("rho0", ctypes.c_double), ("allow_inexact", ctypes.c_int), ("log_every", ctypes.c_int),
+                ("mu_exponent", ctypes.c_double), ("prandtl", ctypes.c_double), ("rho0", ctypes.c_double), ("allow_inexact", ctypes.c_int), ("log_every", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
@@ -153,7 +153,7 @@ class Sim:
 
     def __init__(self, shape, dx, velocity_set, hermite_order, tau, dt, interp_order=3, storage="fp64",
                  cs_scale=1.0, compressible=False, gamma=1.4, mu=0.0, rho0=1.0, allow_inexact=False,
-                 log_every=1, kernel="auto", stream=None, mu_exponent=0.0):
+                 log_every=1, kernel="auto", stream=None, mu_exponent=0.0, prandtl=1.0):
         L = lib()
         g = Grid()
         g.dim = len(shape)
@@ -170,6 +170,7 @@ class Sim:
         o.gamma = float(gamma)
         o.mu = float(mu)
         o.mu_exponent = float(mu_exponent)
+        o.prandtl = float(prandtl)
         o.rho0 = float(rho0)
         o.allow_inexact = int(bool(allow_inexact))
         o.log_every = int(log_every)

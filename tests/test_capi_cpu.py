@@ -70,7 +70,7 @@ def test_default_options_layout(olb):
     o = olb.Options()
     olb.lib().olb_default_options(ctypes.byref(o))
     assert (o.interp_order, o.storage, o.cs_scale, o.compressible) == (3, 0, 1.0, 0)
-    assert (o.gamma, o.mu, o.mu_exponent, o.rho0) == (1.4, 0.0, 0.0, 1.0)
+    assert (o.gamma, o.mu, o.mu_exponent, o.prandtl, o.rho0) == (1.4, 0.0, 0.0, 1.0, 1.0)
     assert (o.allow_inexact, o.log_every, o.kernel, o.stream) == (0, 1, 0, None)
 
 
@@ -87,6 +87,10 @@ def test_default_options_layout(olb):
     (dict(N=3), -7),                            # D3Q27 has degree 5 < 2N = 6
     (dict(vs="D3Q21", compressible=1, mu=0.1), -7),  # c_s = sqrt(3/5) != 1
     (dict(vs="D3Q45", N=4, compressible=1, mu=0.1, mu_exponent=float("nan")), -1),
+    (dict(prandtl=0.75), -1),                   # Pr belongs to the compressible model
+    (dict(vs="D3Q45", N=4, compressible=1, mu=0.1, prandtl=0.0), -1),
+    (dict(vs="D3Q45", N=2, compressible=1, mu=0.1, prandtl=0.75), -7),  # f^eq of N = 2 has a heat flux
+    (dict(vs="D3Q27", N=4, compressible=1, mu=0.1, allow_inexact=1, prandtl=0.75), -7),  # degree 5 < 7
 ])
 def test_argument_checks(olb, kw, code):
     rc, h = _create(olb, **kw)

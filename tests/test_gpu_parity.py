@@ -31,15 +31,16 @@ def olb():
 
 
 def make_pair(olb, name, shape, N=2, p=4, storage="fp64", comp=False, courant=0.4, cs_scale=1.0, tau=0.7,
-              mu=0.02, gamma=1.4, seed=1, kernel="auto", mu_exponent=0.0):
+              mu=0.02, gamma=1.4, seed=1, kernel="auto", mu_exponent=0.0, prandtl=1.0):
     vs = V.get(name)
     if cs_scale != 1.0:
         vs = vs.scaled(cs_scale)
     dx = 0.05
     dt = courant * dx / np.abs(vs.xi).max()
-    prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=tau, compressible=comp, gamma=gamma, mu=mu, mu_exponent=mu_exponent)
+    prm = O.Params(vs, N, p, dt=dt, dx=dx, tau=tau, compressible=comp, gamma=gamma, mu=mu, mu_exponent=mu_exponent,
+                   prandtl=prandtl)
     sim = olb.Sim(shape, dx, name, N, tau, dt, interp_order=p, storage=storage, cs_scale=cs_scale,
-                  compressible=comp, gamma=gamma, mu=mu, kernel=kernel, mu_exponent=mu_exponent)
+                  compressible=comp, gamma=gamma, mu=mu, kernel=kernel, mu_exponent=mu_exponent, prandtl=prandtl)
     rng = np.random.default_rng(seed)
     grid = tuple(reversed(shape))
     rho = 1.0 + 0.05 * rng.uniform(-1, 1, grid)
@@ -168,9 +169,40 @@ def test_one_step_parity_viscosity_power_law(olb, name, shape, p, storage, kerne
     _one_step(olb, name, shape, 4, p, storage, True, 0.4, 1.0, kernel, mu_exponent=omega)
 
 
-def _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel, mu_exponent=0.0):
+PRANDTL = [
+    ("D2Q19", (40, 70), 4, "fp64", "auto", 0.75, 0.0),
+    ("D2Q25", (40, 70), 4, "fp32", "auto", 0.75, 0.0),
+    ("D2Q19", (33, 70), 3, "fp32", "auto", 2.0, 0.7),
+    ("D3Q45", (34, 10, 9), 4, "fp64", "auto", 0.75, 0.0),
+    ("D3Q45", (32, 16, 10), 4, "fp32", "auto", 0.75, 0.0),
+    ("D3Q45", (32, 16, 10), 3, "fp32", "auto", 0.5, 0.7),
+    ("D3Q45", (32, 16, 10), 4, "bf16", "auto", 0.75, 0.0),
+    ("D3Q45", (32, 16, 10), 4, "fp16", "auto", 0.75, 0.0),
+    ("D3Q45", (16, 12, 10), 4, "fp32", "generic", 0.75, 0.0),
+    ("D3Q45", (16, 12, 10), 4, "fp64", "generic", 1.6, 0.0),
+    ("D2Q25", (36, 20), 5, "fp64", "generic", 0.75, 0.0),
+]
+
+
+@pytest.mark.parametrize("name,shape,p,storage,kernel,pr,omega", PRANDTL)
+def test_one_step_parity_prandtl(olb, name, shape, p, storage, kernel, pr, omega):
+    """Compressible step with the heat-flux quasi-equilibrium (Pr != 1) in
+    every kernel and storage that runs the compressible collision."""
+    _one_step(olb, name, shape, 4, p, storage, True, 0.4, 1.0, kernel, mu_exponent=omega, prandtl=pr)
+
+
+def test_ten_steps_prandtl_fp64(olb):
+    sim, prm, state = make_pair(olb, "D3Q45", (32, 16, 10), N=4, p=4, comp=True, prandtl=0.75)
+    want, _ = oracle_steps(prm, state, steps=10)
+    sim.step(10)
+    got = sim.get_populations(np.zeros_like(state))
+    assert rel_err(got, want, np.zeros(state.shape[0]), "fp64") < 1e-11
+    sim.close()
+
+
+def _one_step(olb, name, shape, N, p, storage, comp, courant, cs, kernel, mu_exponent=0.0, prandtl=1.0):
     sim, prm, state = make_pair(olb, name, shape, N=N, p=p, storage=storage, comp=comp, courant=courant,
-                                cs_scale=cs, kernel=kernel, mu_exponent=mu_exponent)
+                                cs_scale=cs, kernel=kernel, mu_exponent=mu_exponent, prandtl=prandtl)
     want, diag = oracle_steps(prm, state)
     sim.step(1)
     got = sim.get_populations(np.zeros_like(state))
