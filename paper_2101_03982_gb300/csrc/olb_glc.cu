@@ -55,13 +55,13 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v;
 }
 
-template <typename S, int D>
+template <typename S, int D, int P>
 __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                      const GlcArgs a) {
   using C = typename Store<S>::C;
   constexpr int TY = D == 3 ? GlcTile<C>::TY : 32;
   constexpr int TZ = D == 3 ? GlcTile<C>::TZ : 1;
-  constexpr int WS = GLC_PMAX + 1;
+  constexpr int WS = GLC_PMAX + 1, P1 = P + 1, NW = GT / 32;
   extern __shared__ unsigned char smem_raw[];
   C* wsm = reinterpret_cast<C*>(smem_raw);  // [3][GLC_PMAX][WS] weights of this velocity
   C* b0 = wsm + 3 * GLC_PMAX * WS;
@@ -71,7 +71,6 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   const int tile = (int)(blockIdx.x % (unsigned)a.ntiles);
   const int plane = (int)(blockIdx.x / (unsigned)a.ntiles);
   const int i = plane % a.Q;
-  const int p = a.p, p1 = a.p + 1;
   const int tx = tile % a.nt[0], tr = tile / a.nt[0];
   const int x0 = tx * GTX, y0 = (tr % a.nt[1]) * TY, z0 = (tr / a.nt[1]) * TZ;
   const int act = a.active[i];
@@ -82,53 +81,74 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   const int n0 = a.pad.n[0], n1 = a.pad.n[1], n2 = a.pad.n[2];
 
   const C* __restrict__ W = static_cast<const C*>(a.W);
-  for (int t = threadIdx.x; t < 3 * p * p1; t += GT) {
-    const int ax = t / (p * p1), r = t - ax * (p * p1), k = r / p1, m = r - k * p1;
+  for (int t = threadIdx.x; t < 3 * P * P1; t += GT) {
+    const int ax = t / (P * P1), r = t - ax * (P * P1), k = r / P1, m = r - k * P1;
     wsm[(ax * GLC_PMAX + k) * WS + m] = W[((size_t)(i * 3 + ax) * GLC_PMAX + k) * WS + m];
   }
 
   // the tile and its reach, rows along x: asynchronous element copies (no
-  // register round trip, so every copy of the CTA is in flight at once)
+  // register round trip, so every copy of the CTA is in flight at once); the
+  // row index (yb, zb) advances by NW rows per iteration without a division
   static_assert(std::is_same<S, C>::value, "the GLC pull stages the storage type as is");
   const S* __restrict__ sp = src + (size_t)plane * a.pad.plane;
   const unsigned b0s = smem_u32(b0);
-  for (int r = warp; r < ey * ez; r += GT / 32) {
-    const int yb = r % ey, zb = r / ey;
+  const bool xin = x0 - lox >= 0 && x0 - lox + ex <= n0;  // no wrap along x
+  int yb = warp, zb = 0;
+  while (yb >= ey) {
+    yb -= ey;
+    ++zb;
+  }
+  for (int r = warp; r < ey * ez; r += NW) {
     const S* __restrict__ row = sp + pad_index(a.pad, 0, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0);
-    for (int xb = lane; xb < ex; xb += 32)
-      cp_async_elem<sizeof(S)>(b0s + (unsigned)((r * ex + xb) * sizeof(S)), row + wrap(x0 - lox + xb, n0));
+    const unsigned drow = b0s + (unsigned)(r * ex * (int)sizeof(S));
+    if (xin) {
+      const S* __restrict__ rx = row + (x0 - lox);
+      for (int xb = lane; xb < ex; xb += 32) cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), rx + xb);
+    } else {
+      for (int xb = lane; xb < ex; xb += 32)
+        cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), row + wrap(x0 - lox + xb, n0));
+    }
+    yb += NW;
+    while (yb >= ey) {
+      yb -= ey;
+      ++zb;
+    }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
 
   C* cur = b0;
   C* nxt = b1;
-  int cx = ex, cy = ey;
-  if (act & 1) {  // x pass: (ex, ey, ez) -> (GTX, ey, ez)
-    const int k = (x0 + lane) % p;
-    const int f = a.first[(i * 3 + 0) * GLC_PMAX + k] + lox + lane;
-    const C* w = wsm + (0 * GLC_PMAX + k) * WS;
-    for (int r = warp; r < ey * ez; r += GT / 32) {
-      const C* s = cur + r * cx + f;
-      C acc = C(0);
-      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m], acc);
+  int cy = ey;
+  if (act & 1) {  // x pass: (ex, ey, ez) -> (GTX, ey, ez); the residue depends on the lane only
+    const int k = (x0 + lane) % P;
+    const C* s0 = cur + a.first[(i * 3 + 0) * GLC_PMAX + k] + lox + lane;
+    C w[P1];
+#pragma unroll
+    for (int m = 0; m < P1; ++m) w[m] = wsm[(0 * GLC_PMAX + k) * WS + m];
+#pragma unroll 4
+    for (int r = warp; r < ey * ez; r += NW) {
+      const C* s = s0 + r * ex;
+      C acc = w[0] * s[0];
+#pragma unroll
+      for (int m = 1; m < P1; ++m) acc = fma(w[m], s[m], acc);
       nxt[r * GTX + lane] = acc;
     }
     C* t = cur;
     cur = nxt;
     nxt = t;
-    cx = GTX;
     __syncthreads();
   }
   if (act & 2) {  // y pass: (GTX, ey, ez) -> (GTX, TY, ez)
-    for (int r = warp; r < TY * ez; r += GT / 32) {
+#pragma unroll 2
+    for (int r = warp; r < TY * ez; r += NW) {
       const int oy = r % TY, oz = r / TY;
-      const int k = (y0 + oy) % p;
-      const int f = a.first[(i * 3 + 1) * GLC_PMAX + k] + loy + oy;
+      const int k = (y0 + oy) % P;
       const C* w = wsm + (1 * GLC_PMAX + k) * WS;
-      const C* s = cur + (oz * cy + f) * GTX + lane;
-      C acc = C(0);
-      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m * GTX], acc);
+      const C* s = cur + (oz * cy + a.first[(i * 3 + 1) * GLC_PMAX + k] + loy + oy) * GTX + lane;
+      C acc = w[0] * s[0];
+#pragma unroll
+      for (int m = 1; m < P1; ++m) acc = fma(w[m], s[m * GTX], acc);
       nxt[(oz * TY + oy) * GTX + lane] = acc;
     }
     C* t = cur;
@@ -137,22 +157,22 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
     cy = TY;
     __syncthreads();
   }
-  (void)cx;
   // z pass (or the plain copy of the passes' result) into the padded interior
   S* __restrict__ dp = dst + (size_t)plane * a.pad.plane;
   const int gx = x0 + lane;
   const bool zpass = D == 3 && (act & 4);
-  for (int r = warp; r < TY * TZ; r += GT / 32) {
+#pragma unroll 2
+  for (int r = warp; r < TY * TZ; r += NW) {
     const int oy = r % TY, oz = r / TY;
     const int gy = y0 + oy, gz = z0 + oz;
     C v;
     if (zpass) {
-      const int k = gz % p;
-      const int f = a.first[(i * 3 + 2) * GLC_PMAX + k] + loz + oz;
+      const int k = gz % P;
       const C* w = wsm + (2 * GLC_PMAX + k) * WS;
-      const C* s = cur + (f * cy + oy) * GTX + lane;
-      C acc = C(0);
-      for (int m = 0; m < p1; ++m) acc = fma(w[m], s[m * cy * GTX], acc);
+      const C* s = cur + ((a.first[(i * 3 + 2) * GLC_PMAX + k] + loz + oz) * cy + oy) * GTX + lane;
+      C acc = w[0] * s[0];
+#pragma unroll
+      for (int m = 1; m < P1; ++m) acc = fma(w[m], s[m * cy * GTX], acc);
       v = acc;
     } else {
       v = cur[(oz * cy + oy) * GTX + lane];
@@ -167,9 +187,19 @@ int launch_typed(const GlcArgs& a, const void* src, void* dst, void* stream) {
   const size_t bytes = glc_smem_bytes(a, sizeof(C));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const unsigned blocks = (unsigned)a.planes * (unsigned)a.ntiles;
-  auto k2 = glc_pull_kernel<S, 2>;
-  auto k3 = glc_pull_kernel<S, 3>;
-  auto kern = a.D == 2 ? k2 : k3;
+  void (*kern)(const S*, S*, const GlcArgs) = nullptr;
+  switch (a.p) {
+#define OLB_GLC_CASE(PP) \
+  case PP: kern = a.D == 2 ? glc_pull_kernel<S, 2, PP> : glc_pull_kernel<S, 3, PP>; break;
+    OLB_GLC_CASE(1)
+    OLB_GLC_CASE(2)
+    OLB_GLC_CASE(3)
+    OLB_GLC_CASE(4)
+    OLB_GLC_CASE(5)
+    OLB_GLC_CASE(6)
+#undef OLB_GLC_CASE
+    default: return -1;  // orders above the step kernels' are not built
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return (int)e;
   kern<<<blocks, GT, bytes, s>>>(static_cast<const S*>(src), static_cast<S*>(dst), a);
