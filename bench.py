@@ -355,7 +355,7 @@ def adjoint_table(torch):
         rho, u = inputs.tgv3d(n, rp.u0, rp.cs ** 2)
         sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
         K = 25
-        sim.tape_reserve(K + 1)
+        sim.tape_reserve(K)
         lam = torch.randn((sim.Q, n, n, n), dtype=getattr(torch, sim.adjoint_dtype), device="cuda")
         stream = torch.cuda.current_stream()
 

@@ -297,15 +297,18 @@ int olb_set_wait_polls(olb_handle h, long long polls);
  * unshifted populations.  on_device = 1: device pointers on the handle's stream (the call is
  * asynchronous); 0: host pointers (the call completes and checks the device error flag).
  *
- * olb_tape_reserve  allocate nslots padded state slots on the device (kept until destroy).
- * olb_tape_record   slot 0 = current state, then n forward steps, step s writing slot s;
- *                   the handle's state advances by n steps.  Needs n + 1 <= nslots.
+ * olb_tape_reserve  allocate nslots tape slots on the device (kept until destroy).  A slot holds
+ *                   the pulled populations f~ of one step (Q values per node, adjoint type),
+ *                   the input of that step's collision, which is all its adjoint needs.
+ * olb_tape_record   n forward steps of the handle's state (it advances by n steps), step s
+ *                   keeping its pulled populations in slot s - 1.  Needs n <= nslots.
  * olb_tape_adjoint  lambda in: dJ/d(state after the last recorded step); lambda out:
  *                   dJ/d(state n steps earlier), 1 <= n <= recorded steps.  n + 1 launches of
  *                   the adjoint kernel plus one scatter and one gather.
  * olb_adjoint_step  one step: fwd_state is the state before the step in the olb_get_state
  *                   layout (olb_state_bytes bytes); lambda in: dJ/d(state after the step),
- *                   out: dJ/d(fwd_state).  Uses tape slot 0 (clears a recorded trajectory).
+ *                   out: dJ/d(fwd_state).  Runs one recorded forward step from fwd_state into
+ *                   tape slot 0 (clears a recorded trajectory); the handle's state is kept.
  * olb_moments_vjp   seed of a sweep from dJ/drho and dJ/du at the handle's current state:
  *                   lambda_i = dJ/drho + dJ/du . (xi_i - u) / rho.  grad_rho [n] and grad_u
  *                   [D][n] (FP64, either may be NULL = zero).

@@ -13,7 +13,8 @@ torch, with every vector-Jacobian product evaluated by the library's kernels:
   (olb_tape_adjoint); finally the gradient through the initial equilibrium
   (olb_equilibrium_vjp).
 
-Memory: nsteps/every compact checkpoints plus every + 1 padded tape slots.
+Memory: nsteps/every compact checkpoints plus `every` tape slots (the pulled
+populations of one step each).
 The recomputation costs one extra forward pass in total.
 """
 import torch
@@ -56,7 +57,7 @@ class SimFunction(torch.autograd.Function):
         gr = g_rho.contiguous() if g_rho is not None else None
         gu = g_u.contiguous() if g_u is not None else None
         sim.moments_vjp(gr, gu, lam)
-        sim.tape_reserve(ctx.every + 1)
+        sim.tape_reserve(ctx.every)
         for buf, k in reversed(ctx.ckpts):
             sim.set_state(buf)
             sim.tape_record(k)

@@ -78,8 +78,8 @@ struct olb_ctx {
   std::vector<double> W;      // [Q][3][p+1]
   // adjoint: tape of forward states (padded, like buf) and the adjoint buffers
   std::vector<void*> tape;
-  std::vector<TmaMaps> tape_maps;  // m[0] of each slot (the forward kernel's boxes)
-  std::vector<TmaMaps> tape_amaps; // m[0] of each slot (the adjoint kernel's boxes)
+  // slot s: the pulled populations f~ of recorded step s + 1 in the two-phase
+  // kernel's tile order [tile][Q][tile nodes], arithmetic type
   int tape_len = 0;                // slots holding a recorded state
   void* adj[2] = {nullptr, nullptr};
   TmaMaps adj_maps{};              // m[k] of adj[k]
@@ -87,7 +87,7 @@ struct olb_ctx {
   int adj_grid = 0, adj_nt[3] = {0, 0, 0}, adj_ntiles = 0;
   void* adj_scratch = nullptr;
   std::vector<unsigned char> st_refl, st_id;  // reflected and identity stencils
-  WgSchedule sched_adj[3]{};       // first step, middle steps, last (pull only)
+  WgSchedule sched_adj{};          // the adjoint planes Q..2Q-1 of every launch
   int adj_ready = 0;
   // enstrophy diagnostic: velocity field and per-block partials
   double* ens_u = nullptr;
@@ -650,35 +650,24 @@ int adj_prepare(olb_ctx* h) {
     cudaError_t e = cudaMalloc(&h->adj_scratch, sb);
     if (e != cudaSuccess) return fail(OLB_ENOMEM, "adjoint staging: " + std::string(cudaGetErrorString(e)));
   }
-  std::vector<std::pair<double, int>> first, mid, last;
-  for (int i = 0; i < h->Q; ++i) {
-    const double c = plane_cost(h, i);
-    first.push_back({c, i});
-    first.push_back({1.0, h->Q + i});
-    mid.push_back({c, i});
-    mid.push_back({c, h->Q + i});
-    last.push_back({c, h->Q + i});
-  }
-  lpt_schedule(h->ainfo.wg, first, &h->sched_adj[0]);
-  lpt_schedule(h->ainfo.wg, mid, &h->sched_adj[1]);
-  lpt_schedule(h->ainfo.wg, last, &h->sched_adj[2]);
-  // forward-state maps of the tape slots made before the adjoint was prepared
-  for (size_t s = h->tape_amaps.size(); s < h->tape.size(); ++s) {
-    h->tape_amaps.emplace_back();
-    const int rc = encode_maps(h, h->tape[s], h->planes, h->tape_amaps.back().m[0], h->ainfo);
-    if (rc) return rc;
-  }
+  // every launch stages the adjoint planes only (the forward populations
+  // come from the tape)
+  std::vector<std::pair<double, int>> adj_planes;
+  for (int i = 0; i < h->Q; ++i) adj_planes.push_back({plane_cost(h, i), h->Q + i});
+  lpt_schedule(h->ainfo.wg, adj_planes, &h->sched_adj);
   h->adj_ready = 1;
   return OLB_OK;
 }
 
 // One launch of the adjoint kernel: adjoint input adj[in], output adj[out],
-// forward state `fwd` (a tape slot; null in mode 2).
-int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, const WgSchedule* sch, int slot, int in,
-               int out) {
+// pulled forward populations of tape slot `slot` (mode 1; -1 in mode 2).
+// Only the adjoint planes are staged (sched_adj); phase B reads f~ from the
+// slot.
+int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, int slot, int in, int out) {
   StepLaunch L = base_launch(h);
-  L.a.buf[0] = slot >= 0 ? h->tape[slot] : h->adj[in];
+  L.a.buf[0] = h->adj[in];
   L.a.buf[1] = h->adj[out];
+  L.a.slab = slot >= 0 ? h->tape[slot] : nullptr;
   L.a.src = 0;
   L.a.scratch = h->adj_scratch;
   L.a.planes = 2 * h->Q;
@@ -688,11 +677,11 @@ int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, cons
   L.a.ntiles = h->adj_ntiles;
   L.grid = h->adj_grid;
   TmaMaps M;
-  std::memcpy(M.m[0], slot >= 0 ? h->tape_amaps[slot].m[0] : h->adj_maps.m[in], sizeof(M.m[0]));
+  std::memcpy(M.m[0], h->adj_maps.m[in], sizeof(M.m[0]));
   std::memcpy(M.m[1], h->adj_maps.m[in], sizeof(M.m[1]));
   L.stentab2 = st2.data();
   L.maps = &M;
-  L.sched = sch;
+  L.sched = &h->sched_adj;
   int r;
   if (h->storage == OLB_FP64) r = h->D == 2 ? launch_adj_f64_2d(L) : launch_adj_f64_3d(L);
   else r = h->D == 2 ? launch_adj_f32_2d(L) : launch_adj_f32_3d(L);
@@ -708,18 +697,20 @@ int adjoint_sweep(olb_ctx* h, const std::vector<int>& slots, void* lam_dev) {
   int cur = 0;
   for (size_t k = 0; k < slots.size(); ++k) {
     const bool first = k == 0;
-    rc = adj_launch(h, 1, first ? h->st_id : h->st_refl, &h->sched_adj[first ? 0 : 1], slots[k], cur, cur ^ 1);
+    rc = adj_launch(h, 1, first ? h->st_id : h->st_refl, slots[k], cur, cur ^ 1);
     if (rc) return rc;
     cur ^= 1;
   }
-  rc = adj_launch(h, 2, h->st_refl, &h->sched_adj[2], -1, cur, cur ^ 1);
+  rc = adj_launch(h, 2, h->st_refl, -1, cur, cur ^ 1);
   if (rc) return rc;
   cur ^= 1;
   return launch_rc(launch_gather(h->aux, h->adj[cur], lam_dev, h->stream), "adjoint gather");
 }
 
+// Tape slots (after adj_prepare): the pulled populations of one step in the
+// two-phase kernel's tile order.
 int tape_grow(olb_ctx* h, int nslots) {
-  const size_t bytes = (size_t)h->planes * h->pad.plane * h->elem;
+  const size_t bytes = (size_t)h->adj_ntiles * h->Q * h->ainfo.tile * adj_elem(h);
   while ((int)h->tape.size() < nslots) {
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -729,16 +720,28 @@ int tape_grow(olb_ctx* h, int nslots) {
       return fail(OLB_ENOMEM, "tape slot: " + std::string(cudaGetErrorString(e)));
     }
     h->tape.push_back(p);
-    h->tape_maps.emplace_back();
-    int rc = encode_maps(h, p, h->planes, h->tape_maps.back().m[0], h->info);
-    if (rc) return rc;
-    if (h->adj_ready) {
-      h->tape_amaps.emplace_back();
-      rc = encode_maps(h, p, h->planes, h->tape_amaps.back().m[0], h->ainfo);
-      if (rc) return rc;
-    }
   }
   return OLB_OK;
+}
+
+// One forward step of the two-phase kernel from padded buffer `src` (maps
+// `m`) into `dst` that also stores its pulled populations in tape slot `slot`.
+int record_step(olb_ctx* h, void* src, const CUtensorMap* m, void* dst, int slot) {
+  StepLaunch L = base_launch(h);
+  L.force_generic = 2;
+  L.a.reduce = 0;
+  L.a.src = 0;
+  L.a.buf[0] = src;
+  L.a.buf[1] = dst;
+  L.a.slab = h->tape[slot];
+  for (int k = 0; k < 3; ++k) L.a.nt[k] = h->adj_nt[k];
+  L.a.ntiles = h->adj_ntiles;
+  L.grid = h->adj_grid;
+  TmaMaps M;
+  std::memcpy(M.m[0], m, sizeof(M.m[0]));
+  std::memcpy(M.m[1], m, sizeof(M.m[1]));
+  L.maps = &M;
+  return launch_rc(launch_step(h->storage, h->D, L), "sl_step (recorded)");
 }
 
 }  // namespace
@@ -1531,24 +1534,19 @@ int olb_tape_record(olb_handle h, int n) {
   if (h->xbc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for periodic grids only");
   if (h->glc) return fail(OLB_EUNSUPPORTED, "the adjoint is built for the uniform-grid interpolation only");
   if (n < 0) return fail(OLB_EINVAL, "negative step count");
-  if (n + 1 > (int)h->tape.size()) return fail(OLB_EBOUNDS, "tape has fewer than n + 1 slots");
+  if (n > (int)h->tape.size()) return fail(OLB_EBOUNDS, "tape has fewer than n slots");
   int rc = set_device(h);
   if (rc) return rc;
-  const size_t bytes = (size_t)h->planes * h->pad.plane * h->elem;
-  cudaError_t e = cudaMemcpyAsync(h->tape[0], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "tape copy");
-  StepLaunch L = base_launch(h);
-  L.a.reduce = 0;
-  L.a.src = 0;
+  rc = adj_prepare(h);
+  if (rc) return rc;
+  if (h->state_bad) return fail(OLB_ETIMEOUT, "the state is invalid after a wait ran out: set it again");
+  // the state advances through the handle's buffers; step s also keeps its
+  // pulled populations in slot s - 1
   for (int s = 1; s <= n; ++s) {
-    L.a.buf[0] = h->tape[s - 1];
-    L.a.buf[1] = h->tape[s];
-    L.maps = &h->tape_maps[s - 1];
-    rc = launch_rc(launch_step(h->storage, h->D, L), "sl_step (tape)");
+    rc = record_step(h, h->buf[h->cur], h->maps.m[h->cur], h->buf[h->cur ^ 1], s - 1);
     if (rc) return rc;
+    h->cur ^= 1;
   }
-  e = cudaMemcpyAsync(h->buf[h->cur], h->tape[n], bytes, cudaMemcpyDeviceToDevice, h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "tape copy");
   h->step_count += n;
   h->partials_valid = 0;
   h->tape_len = n + 1;
@@ -1600,8 +1598,12 @@ int olb_adjoint_step(olb_handle h, const void* fwd_state, void* lambda, int on_d
   }
   const void* fs = on_device ? fwd_state : tmp;
   void* lam = on_device ? lambda : static_cast<char*>(tmp) + sbytes;
-  rc = launch_rc(launch_scatter(h->aux, h->tape[0], fs, h->stream), "adjoint state scatter");
+  // the forward step from fwd_state (in adj[1], ghosts filled by the scatter)
+  // into adj[0] records its pulled populations in slot 0; the adjoint
+  // buffers are free until the sweep starts
+  rc = launch_rc(launch_scatter(h->aux, h->adj[1], fs, h->stream), "adjoint state scatter");
   h->tape_len = 0;  // slot 0 no longer holds a recorded trajectory
+  if (rc == OLB_OK) rc = record_step(h, h->adj[1], h->adj_maps.m[1], h->adj[0], 0);
   if (rc == OLB_OK) rc = adjoint_sweep(h, std::vector<int>{0}, lam);
   if (!on_device) {
     if (rc == OLB_OK) rc = copy_out(h, lambda, lam, lbytes, 0);

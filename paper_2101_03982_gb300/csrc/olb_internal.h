@@ -88,6 +88,8 @@ struct StepArgs {
   void* buf[2];         // population buffers (padded planes)
   int src;              // index of the current state in buf
   void* scratch;        // per-CTA staging of pulled populations
+  void* slab;           // tape slab [tile][Q][tile nodes] of a recorded step: the forward step writes
+                        // its pulled populations there, the adjoint reads them (null otherwise)
   double* partials;     // per-CTA reduction partials [grid][NRED]
   int* err;             // device error flag (1: a bounded wait ran out)
   long long wait_polls; // bound of the waits for staging copies (polls of the barrier)

@@ -239,6 +239,11 @@ __device__ __forceinline__ void st4p(C* p, T lo, T hi) {
   st4(p, v);
 }
 
+// L2 prefetch of `bytes` (multiple of 16, 16-byte aligned address) of global memory.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
 // global to shared memory, completing on the mbarrier.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -412,6 +417,9 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   const int nplan = sched.n[wg];
   S* __restrict__ dst = static_cast<S*>(a.buf[a.src ^ 1]);
   C* __restrict__ scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE;
+  // a forward step recorded for the adjoint stages the pulled values of tile t
+  // in the tape slab [t][plane][TILE] (kept), the adjoint reads them there
+  C* const slab = static_cast<C*>(a.slab);
   const unsigned long long keep = policy_evict_last();
 
   // stencil table, tensor maps and tensor plane of a staged plane
@@ -499,6 +507,12 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
                       pd.n[2] >= pd.gl[2] + pd.gr[2];
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    if (!ADJ && slab) scr = slab + (size_t)tile * planes * L::TILE;
+    // the pulled forward populations f~ of the tile (adjoint): staged planes
+    // q < Q, or the tape slab of the recorded step
+    const C* __restrict__ fws = (ADJ && slab) ? slab + (size_t)tile * Q * L::TILE : scr;
+    // the tape values of the tile are read by phase B: bring them into L2 now
+    if (ADJ && slab && a.mode == 1 && tid < Q) bulk_prefetch_l2(fws + (size_t)tid * L::TILE, L::TILE * sizeof(C));
     // ---------------- phase A: pull every plane of the tile -----------------
     if constexpr (L::TWOBOX) {
       for (int k = 0; k < nplan && !failed; ++k) {
@@ -1329,7 +1343,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
-        const float2 ft = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(scr) + (size_t)i * L::TILE + n);
+        const float2 ft = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(fws) + (size_t)i * L::TILE + n);
         A = add2(A, ft);
         jx = fma2(f2(vt.xi[i][0]), ft, jx);
         jy = fma2(f2(vt.xi[i][1]), ft, jy);
@@ -1408,7 +1422,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= Q) break;
-        const C ft = scr[(size_t)i * L::TILE + n];
+        const C ft = fws[(size_t)i * L::TILE + n];
         A += ft;
         jx = fma(vt.xi[i][0], ft, jx);
         jy = fma(vt.xi[i][1], ft, jy);

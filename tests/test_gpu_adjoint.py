@@ -142,7 +142,7 @@ def test_unsupported_configurations_are_rejected(olb):
     sim, _, _ = make_pair(olb, "D3Q27", (16, 8, 8), N=2, p=4, storage="fp64")
     sim.tape_reserve(3)
     with pytest.raises(olb.OlbError) as e:
-        sim.tape_record(3)  # needs 4 slots
+        sim.tape_record(4)  # needs 4 slots
     assert e.value.code == -6
     sim.close()
 
