@@ -336,7 +336,7 @@ def precision_comp_table(torch, n, steps):
                  fp64_seconds=round(t64, 1))]
 
 
-def adjoint_table(torch):
+def adjoint_table(torch, configs=((64, "fp32"), (64, "fp64"), (128, "fp32"))):
     """Adjoint of the isothermal step against the forward step (CUDA events).
 
     D3Q27, N = 2, p = 3, Re = 400, Ma = 0.1 (the adjoint workload) at 64^3
@@ -348,7 +348,7 @@ def adjoint_table(torch):
     """
     from paper_2101_03982_gb300 import inputs, olb, params
     rows = []
-    for n, storage in ((64, "fp32"), (64, "fp64"), (128, "fp32")):
+    for n, storage in configs:
         rp = params.tgv_isothermal("D3Q27", n, 400.0, 0.1, 0.4)
         sim = olb.Sim((n,) * 3, rp.dx, "D3Q27", 2, rp.tau, rp.dt, interp_order=3, storage=storage,
                       cs_scale=rp.cs_scale, log_every=1000000)
@@ -571,6 +571,8 @@ def main():
     ap.add_argument("--precision-comp-steps", type=int, default=0,
                     help="steps of the compressible D3Q45 FP32-vs-FP64 k history (0: skip; minutes of FP64)")
     ap.add_argument("--precision-comp-n", type=int, default=128, help="grid of that comparison")
+    ap.add_argument("--adjoint-only", default=None, metavar="N:STORAGE",
+                    help="only time the adjoint (tape record and sweep) at N^3 with that storage, e.g. 128:fp32")
     ap.add_argument("--workload", default="d3q27", choices=sorted(WORKLOADS),
                     help="timed workload (the reported metric is quoted on the default)")
     args = ap.parse_args()
@@ -584,6 +586,10 @@ def main():
     from paper_2101_03982_gb300 import olb
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.adjoint_only:
+        n, storage = args.adjoint_only.split(":")
+        print(json.dumps({"adjoint": adjoint_table(torch, ((int(n), storage),))}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -214,7 +214,8 @@ int olb_kinetic_energy(olb_handle h, double* k, double* dissipation);
  * the moments of the stored populations and fourth-order central differences of spacing dx on
  * the periodic grid (2D: the z component only).  The scaled enstrophy is nu * E.  Off the
  * per-step path (three launches and a read-back); synchronises the handle's stream.
- * OLB_ENONFINITE if the result is not finite. */
+ * OLB_ENONFINITE if the result is not finite; OLB_EUNSUPPORTED while the inflow/outflow x
+ * boundary is set (the differences are periodic). */
 int olb_enstrophy(olb_handle h, double* enstrophy);
 
 /* The populations f_i (planes Q..2Q-1: g_i) of the stored post-collision
@@ -236,8 +237,8 @@ int olb_set_populations(olb_handle h, const double* f, int on_device);
  * periodic again (every ghost copy rewritten from the interior).  OLB_EINVAL
  * for another kind, a null u, rho <= 0 or a non-finite value (theta <= 0 when
  * compressible).  The adjoint and the tape (olb_tape_*, olb_adjoint_step)
- * return OLB_EUNSUPPORTED while kind 1 is set; olb_enstrophy keeps its
- * periodic differences in x. */
+ * and olb_enstrophy (periodic differences) return OLB_EUNSUPPORTED while
+ * kind 1 is set.  Switching back rewrites the ghosts in place (no allocation). */
 int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, double theta);
 
 /* Raw stored state (checkpoint): exactly olb_state_bytes() bytes, the

@@ -248,6 +248,33 @@ __global__ void __launch_bounds__(AUX_NT) xbc_kernel(const __grid_constant__ Aux
   }
 }
 
+// Periodic ghost copies rewritten in place: one warp per padded (plane, z, y)
+// row; every ghost cell takes the interior value of its periodic image.  Only
+// interior cells are read and only ghost cells are written, so the rows can
+// run in any order.
+template <typename S>
+__global__ void __launch_bounds__(AUX_NT) periodic_ghost_kernel(const __grid_constant__ AuxArgs a, S* state) {
+  const Padded& P = a.pad;
+  const long long rows_pp = (long long)P.np[1] * P.np[2];
+  const long long rows = (long long)a.planes * rows_pp;
+  const long long nw = (long long)gridDim.x * (AUX_NT / 32);
+  const int lane = threadIdx.x & 31;
+  auto image = [](int c, int n) { return ((c % n) + n) % n; };
+  for (long long row = blockIdx.x * (long long)(AUX_NT / 32) + (threadIdx.x >> 5); row < rows; row += nw) {
+    const int p = (int)(row / rows_pp);
+    const long long r = row - (long long)p * rows_pp;
+    const int yy = (int)(r % P.np[1]) - P.gl[1], zz = (int)(r / P.np[1]) - P.gl[2];
+    const bool ghost_row = yy < 0 || yy >= P.n[1] || zz < 0 || zz >= P.n[2];
+    S* plane = state + (long long)p * P.plane;
+    S* line = plane + r * P.np[0];
+    const S* src = plane + pad_index(P, 0, image(yy, P.n[1]), image(zz, P.n[2]));
+    for (int k = lane; k < P.np[0]; k += 32) {
+      const int xx = k - P.gl[0];
+      if (ghost_row || xx < 0 || xx >= P.n[0]) line[k] = src[image(xx, P.n[0])];
+    }
+  }
+}
+
 // Seed of the adjoint sweep: lam_i = dJ/df_i for J(rho, u) given dJ/drho and
 // dJ/du per node, with rho = sum f (Sec. 3) and d u/d f_i = (xi_i - u)/rho.
 template <typename S, typename C>
@@ -468,6 +495,15 @@ int launch_xbc_values(const AuxArgs& a, const XInflow& in, void* vals, void* str
   return by_storage(a.storage, [&](auto tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     xbc_values_kernel<S><<<(a.planes + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, in, (S*)vals);
+    return (int)cudaGetLastError();
+  });
+}
+
+int launch_periodic_ghosts(const AuxArgs& a, void* state, void* stream) {
+  return by_storage(a.storage, [&](auto tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    const long long rows = (long long)a.planes * a.pad.np[1] * a.pad.np[2];
+    periodic_ghost_kernel<S><<<aux_grid(rows * 32), AUX_NT, 0, (cudaStream_t)stream>>>(a, (S*)state);
     return (int)cudaGetLastError();
   });
 }

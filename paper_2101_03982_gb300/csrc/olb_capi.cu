@@ -1223,6 +1223,7 @@ int olb_reductions(olb_handle h, double out[8]) {
 
 int olb_enstrophy(olb_handle h, double* enstrophy) {
   if (!h || !enstrophy) return fail(OLB_EINVAL, "null handle or output");
+  if (h->xbc) return fail(OLB_EUNSUPPORTED, "the enstrophy takes periodic differences: not defined with a non-periodic x");
   int rc = set_device(h);
   if (rc) return rc;
   const int slots = 1024;
@@ -1403,15 +1404,9 @@ int olb_set_x_boundary(olb_handle h, int kind, double rho, const double* u, doub
     return apply_xbc(h, h->buf[h->cur]);
   }
   if (!h->xbc) return OLB_OK;
-  // back to periodic: rewrite every ghost copy from the interior (the handle
-  // stays non-periodic if that fails)
-  const size_t bytes = (size_t)h->planes * h->nnodes * h->elem;
-  void* tmp = nullptr;
-  rc = dev_alloc(h, &tmp, bytes);
-  if (rc) return rc;
-  rc = launch_rc(launch_gather(h->aux, h->buf[h->cur], tmp, h->stream), "gather");
-  if (rc == OLB_OK) rc = launch_rc(launch_scatter(h->aux, h->buf[h->cur], tmp, h->stream), "scatter");
-  cudaFreeAsync(tmp, h->stream);
+  // back to periodic: rewrite every ghost copy from the interior, in place
+  // (the handle stays non-periodic if that fails)
+  rc = launch_rc(launch_periodic_ghosts(h->aux, h->buf[h->cur], h->stream), "periodic ghosts");
   int r2 = stream_sync(h, 0);
   if (rc == OLB_OK) rc = r2;
   if (rc == OLB_OK) h->xbc = 0;

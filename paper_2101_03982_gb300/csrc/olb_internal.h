@@ -228,6 +228,8 @@ int launch_xbc_values(const AuxArgs& a, const XInflow& in, void* vals, void* str
 // Refill the x ghost columns: the inflow values on the left, copies of the
 // last column on the right (every plane, every padded row).
 int launch_xbc(const AuxArgs& a, void* state, const void* vals, void* stream);
+// Every ghost copy of a state rewritten from its periodic image, in place.
+int launch_periodic_ghosts(const AuxArgs& a, void* state, void* stream);
 // Per-block partial sums of |curl u|^2 (slot 0 of NRED per block) of the
 // velocity u [D][n] (FP64), fourth-order central differences of spacing dx.
 int launch_enstrophy(const AuxArgs& a, const double* u, double dx, double* partials, int grid, void* stream);

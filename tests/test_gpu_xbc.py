@@ -71,18 +71,31 @@ def test_inflow_outflow_steps_match_oracle(olb, name, shape, N, p, storage, comp
     sim.close()
 
 
-def test_back_to_periodic_and_adjoint_refused(olb):
-    sim, prm, state = make_pair(olb, "D3Q27", (37, 11, 9), N=2, p=4, storage="fp32")
+@pytest.mark.parametrize("name,shape,N,storage,comp", [
+    ("D3Q27", (37, 11, 9), 2, "fp32", False),
+    ("D2Q19", (40, 33), 4, "fp64", True),
+])
+def test_back_to_periodic_and_adjoint_refused(olb, name, shape, N, storage, comp):
+    """Switching back to periodic rewrites every ghost copy in place: the next
+    step equals the oracle's periodic step of the same state.  The adjoint and
+    the enstrophy (periodic differences) are refused while x is not periodic."""
+    sim, prm, state = make_pair(olb, name, shape, N=N, p=4, storage=storage, comp=comp)
     rho_in, u_in, th_in = inflow_state(prm)
     sim.set_x_boundary("inflow_outflow", rho_in, u_in, th_in)
+    if not comp:
+        with pytest.raises(olb.OlbError) as e:
+            sim.tape_reserve(2)
+        assert e.value.code == -7
     with pytest.raises(olb.OlbError) as e:
-        sim.tape_reserve(2)
+        sim.enstrophy()
     assert e.value.code == -7
     sim.set_x_boundary("periodic")
-    want = O.step(prm, state)[0]
+    Q = prm.vs.Q
+    f, g = O.step(prm, state[:Q], state[Q:] if comp else None)[:2]
+    want = np.concatenate([f, g]) if comp else f
     sim.step(1)
     got = sim.get_populations(np.zeros_like(state))
-    assert rel_err(got, want, base_of(prm, "fp32", state.shape[0]), "fp32") < TOL["fp32"]
+    assert rel_err(got, want, base_of(prm, storage, state.shape[0]), storage) < TOL[storage]
     with pytest.raises(olb.OlbError) as e:
         sim.set_x_boundary("inflow_outflow", -1.0, u_in, th_in)
     assert e.value.code == -1
