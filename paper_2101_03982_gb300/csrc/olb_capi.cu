@@ -1449,6 +1449,11 @@ int olb_set_interpolation(olb_handle h, int scheme) {
     g.ntiles *= g.nt[a];
   }
   g.box_elems = 0;
+  g.b1_elems = 0;
+  // x reach rounded to whole 16-byte groups, so that every staged row starts
+  // on a 16-byte boundary (the 16-byte staging path)
+  const int VG = 16 / (f64 ? 8 : 4);
+  int exmax = 0;
   for (int i = 0; i < h->Q; ++i) {
     int act = 0, ext[3] = {T[0], T[1], T[2]};
     for (int a = 0; a < h->D; ++a) {
@@ -1466,6 +1471,10 @@ int olb_set_interpolation(olb_handle h, int scheme) {
         lo = std::max(lo, -first[k]);
         hi = std::max(hi, first[k] + h->p);
       }
+      if (a == 0) {
+        lo = (lo + VG - 1) / VG * VG;
+        hi = (T[0] + lo + hi + VG - 1) / VG * VG - T[0] - lo;
+      }
       if (lo > 255 || hi > 255) return fail(OLB_EUNSUPPORTED, "GLC departure points too far for the staged box");
       g.lo[i * 3 + a] = (unsigned char)lo;
       g.hi[i * 3 + a] = (unsigned char)hi;
@@ -1473,7 +1482,10 @@ int olb_set_interpolation(olb_handle h, int scheme) {
     }
     g.active[i] = act;
     g.box_elems = std::max(g.box_elems, ext[0] * ext[1] * ext[2]);
+    g.b1_elems = std::max(g.b1_elems, T[0] * ext[1] * ext[2]);
+    exmax = std::max(exmax, ext[0]);
   }
+  g.vec16 = (h->grid.n[0] % VG == 0 && exmax % VG == 0 && exmax / VG <= 32) ? 1 : 0;
   if (glc_smem_bytes(g, f64 ? 8 : 4) > 227 * 1024)
     return fail(OLB_EUNSUPPORTED, "GLC departure points too far for the staged box (Courant number too large)");
   const size_t bytes = nw * (f64 ? sizeof(double) : sizeof(float));

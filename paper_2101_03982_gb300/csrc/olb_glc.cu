@@ -31,13 +31,16 @@ namespace olb {
 
 namespace {
 
-constexpr int GT = 256;  // threads per CTA (8 warps)
+constexpr int GT = 512;  // threads per CTA (16 warps)
 constexpr int GTX = 32;  // tile width along x: one output per lane
 
+// 3D tiles: the reach of the stencils (up to p nodes on each side) is staged
+// with the tile, so tall tiles keep the staged box a small multiple of it;
+// 2D tiles are GTX x 32
 template <typename C>
 struct GlcTile {
-  static constexpr int TY = 8;
-  static constexpr int TZ = sizeof(C) == 8 ? 4 : 8;  // 3D; 2D tiles are GTX x 32
+  static constexpr int TY = 16;
+  static constexpr int TZ = sizeof(C) == 8 ? 8 : 16;
 };
 
 // one element copied global -> shared without passing through registers
@@ -47,6 +50,11 @@ __device__ __forceinline__ void cp_async_elem(unsigned dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// 16 bytes copied global -> shared (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   extern __shared__ unsigned char smem_raw[];
   C* wsm = reinterpret_cast<C*>(smem_raw);  // [3][GLC_PMAX][WS] weights of this velocity
   C* b0 = wsm + 3 * GLC_PMAX * WS;
-  C* b1 = b0 + a.box_elems;
+  C* b1 = b0 + a.box_elems;  // a.b1_elems: the x pass's output
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = (int)(blockIdx.x % (unsigned)a.ntiles);
@@ -86,32 +94,57 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
     wsm[(ax * GLC_PMAX + k) * WS + m] = W[((size_t)(i * 3 + ax) * GLC_PMAX + k) * WS + m];
   }
 
-  // the tile and its reach, rows along x: asynchronous element copies (no
-  // register round trip, so every copy of the CTA is in flight at once); the
-  // row index (yb, zb) advances by NW rows per iteration without a division
+  // the tile and its reach, rows along x: asynchronous copies (no register
+  // round trip, so every copy of the CTA is in flight at once), 16 bytes at a
+  // time where the grid allows it, else one element at a time; the row index
+  // (yb, zb) advances without a division
   static_assert(std::is_same<S, C>::value, "the GLC pull stages the storage type as is");
   const S* __restrict__ sp = src + (size_t)plane * a.pad.plane;
   const unsigned b0s = smem_u32(b0);
-  const bool xin = x0 - lox >= 0 && x0 - lox + ex <= n0;  // no wrap along x
-  int yb = warp, zb = 0;
-  while (yb >= ey) {
-    yb -= ey;
-    ++zb;
-  }
-  for (int r = warp; r < ey * ez; r += NW) {
-    const S* __restrict__ row = sp + pad_index(a.pad, 0, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0);
-    const unsigned drow = b0s + (unsigned)(r * ex * (int)sizeof(S));
-    if (xin) {
-      const S* __restrict__ rx = row + (x0 - lox);
-      for (int xb = lane; xb < ex; xb += 32) cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), rx + xb);
-    } else {
-      for (int xb = lane; xb < ex; xb += 32)
-        cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), row + wrap(x0 - lox + xb, n0));
+  if (a.vec16) {
+    // 16-byte copies: the box starts on a 16-byte column (the host rounds the
+    // x reach), n0 is a multiple of VG, so a copy never straddles the wrap;
+    // one warp takes 32 / cpr rows per iteration
+    constexpr int VG = 16 / (int)sizeof(S);
+    const int cpr = ex / VG, rpi = 32 / cpr;
+    const int lr = lane / cpr, lc = lane - lr * cpr;
+    if (lr < rpi) {
+      const int gx = wrap(x0 - lox + lc * VG, n0);
+      int row = warp * rpi + lr;
+      int yb = row % ey, zb = row / ey;
+      for (; row < ey * ez; row += NW * rpi) {
+        cp_async16(b0s + (unsigned)((row * ex + lc * VG) * (int)sizeof(S)),
+                   sp + pad_index(a.pad, gx, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0));
+        yb += NW * rpi;
+        while (yb >= ey) {
+          yb -= ey;
+          ++zb;
+        }
+      }
     }
-    yb += NW;
+  } else {
+    const bool xin = x0 - lox >= 0 && x0 - lox + ex <= n0;  // no wrap along x
+    int yb = warp, zb = 0;
     while (yb >= ey) {
       yb -= ey;
       ++zb;
+    }
+    for (int r = warp; r < ey * ez; r += NW) {
+      const S* __restrict__ row = sp + pad_index(a.pad, 0, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0);
+      const unsigned drow = b0s + (unsigned)(r * ex * (int)sizeof(S));
+      if (xin) {
+        const S* __restrict__ rx = row + (x0 - lox);
+        for (int xb = lane; xb < ex; xb += 32)
+          cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), rx + xb);
+      } else {
+        for (int xb = lane; xb < ex; xb += 32)
+          cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), row + wrap(x0 - lox + xb, n0));
+      }
+      yb += NW;
+      while (yb >= ey) {
+        yb -= ey;
+        ++zb;
+      }
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -216,7 +249,7 @@ void glc_tile_shape(int D, int elem, int* tx, int* ty, int* tz) {
 }
 
 size_t glc_smem_bytes(const GlcArgs& a, int elem) {
-  return ((size_t)3 * GLC_PMAX * (GLC_PMAX + 1) + 2 * (size_t)a.box_elems) * (size_t)elem;
+  return ((size_t)3 * GLC_PMAX * (GLC_PMAX + 1) + (size_t)a.box_elems + (size_t)a.b1_elems) * (size_t)elem;
 }
 
 int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream) {

@@ -184,6 +184,8 @@ struct GlcArgs {
   int planes, Q, D, p;
   int nt[3], ntiles;                // tiles per axis (glc_tile_shape) and their product
   int box_elems;                    // largest staged box (tile plus reach) over the velocities
+  int b1_elems;                     // largest output of the x pass (tile width x box height x box depth)
+  int vec16;                        // 1: stage with 16-byte copies (n[0] a multiple of 16 bytes' elements)
   int active[MAXQ];                 // bit a: xi_{i,a} != 0
   int first[MAXQ * 3 * GLC_PMAX];   // [i][a][k]
   unsigned char lo[MAXQ * 3], hi[MAXQ * 3];  // [i][a] reach below and above the tile (0 when inactive)
