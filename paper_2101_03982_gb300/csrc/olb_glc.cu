@@ -172,17 +172,27 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
     nxt = t;
     __syncthreads();
   }
+  // The y and z passes give each warp fixed output rows along the pass's axis
+  // (NW is a multiple of TY and TZ's divisors below), so a warp's residue,
+  // stencil weights and first support row are loaded once.
+  static_assert(TY % NW == 0 || NW % TY == 0, "warps and tile rows");
+  static_assert(NW % TZ == 0, "warps and tile depth");
   if (act & 2) {  // y pass: (GTX, ey, ez) -> (GTX, TY, ez)
-#pragma unroll 2
-    for (int r = warp; r < TY * ez; r += NW) {
-      const int oy = r % TY, oz = r / TY;
+    for (int oy = warp % TY; oy < TY; oy += NW) {
       const int k = (y0 + oy) % P;
-      const C* w = wsm + (1 * GLC_PMAX + k) * WS;
-      const C* s = cur + (oz * cy + a.first[(i * 3 + 1) * GLC_PMAX + k] + loy + oy) * GTX + lane;
-      C acc = w[0] * s[0];
+      C w[P1];
 #pragma unroll
-      for (int m = 1; m < P1; ++m) acc = fma(w[m], s[m * GTX], acc);
-      nxt[(oz * TY + oy) * GTX + lane] = acc;
+      for (int m = 0; m < P1; ++m) w[m] = wsm[(1 * GLC_PMAX + k) * WS + m];
+      const C* s = cur + (a.first[(i * 3 + 1) * GLC_PMAX + k] + loy + oy) * GTX + lane;
+      C* o = nxt + oy * GTX + lane;
+#pragma unroll 4
+      for (int oz = warp / TY; oz < ez; oz += (NW > TY ? NW / TY : 1)) {
+        const C* so = s + oz * cy * GTX;
+        C acc = w[0] * so[0];
+#pragma unroll
+        for (int m = 1; m < P1; ++m) acc = fma(w[m], so[m * GTX], acc);
+        o[oz * TY * GTX] = acc;
+      }
     }
     C* t = cur;
     cur = nxt;
@@ -194,23 +204,30 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   S* __restrict__ dp = dst + (size_t)plane * a.pad.plane;
   const int gx = x0 + lane;
   const bool zpass = D == 3 && (act & 4);
-#pragma unroll 2
-  for (int r = warp; r < TY * TZ; r += NW) {
-    const int oy = r % TY, oz = r / TY;
-    const int gy = y0 + oy, gz = z0 + oz;
-    C v;
-    if (zpass) {
-      const int k = gz % P;
-      const C* w = wsm + (2 * GLC_PMAX + k) * WS;
-      const C* s = cur + ((a.first[(i * 3 + 2) * GLC_PMAX + k] + loz + oz) * cy + oy) * GTX + lane;
-      C acc = w[0] * s[0];
+  {
+    const int oz = warp % TZ, gz = z0 + oz;
+    const int k = gz % P;
+    C w[P1];
 #pragma unroll
-      for (int m = 1; m < P1; ++m) acc = fma(w[m], s[m * cy * GTX], acc);
-      v = acc;
-    } else {
-      v = cur[(oz * cy + oy) * GTX + lane];
+    for (int m = 0; m < P1; ++m) w[m] = zpass ? wsm[(2 * GLC_PMAX + k) * WS + m] : C(0);
+    const int zrow = zpass ? a.first[(i * 3 + 2) * GLC_PMAX + k] + loz + oz : oz;
+    const C* s = cur + zrow * cy * GTX + lane;
+    const bool on = gx < n0 && gz < n2;
+    S* d = dp + pad_index(a.pad, gx, 0, gz);
+#pragma unroll 4
+    for (int oy = warp / TZ; oy < TY; oy += NW / TZ) {
+      const C* so = s + oy * GTX;
+      C v;
+      if (zpass) {
+        C acc = w[0] * so[0];
+#pragma unroll
+        for (int m = 1; m < P1; ++m) acc = fma(w[m], so[m * cy * GTX], acc);
+        v = acc;
+      } else {
+        v = so[0];
+      }
+      if (on && y0 + oy < n1) d[(long long)(y0 + oy) * a.pad.np[0]] = Store<S>::st(v);
     }
-    if (gx < n0 && gy < n1 && gz < n2) dp[pad_index(a.pad, gx, gy, gz)] = Store<S>::st(v);
   }
 }
 
