@@ -11,7 +11,7 @@ stored values it needs from the device state node by node, in FP64.
 
 Cases: the 3D Taylor-Green vortex (Re 1600, Ma 0.1, p = 4, Courant 0.4) with
 D3Q27 in FP32 and FP64 at 128^3 and D3Q45 (N = 2) in FP32 at 256^3, and the
-compressible Taylor-Green vortex (D3Q45, N = 4, f + g, Ma 1.0) in FP32 at 256^3
+compressible Taylor-Green vortex (D3Q45, N = 4, f + g, Ma 1.0, Pr 0.75) in FP32 at 256^3
 and at 512^3, the largest workload (99 GB of A/B buffers).
 Bounds as in the small-grid parity tests: FP32 2e-5 of the largest stored
 deviation, FP64 1e-12 of the largest population.
@@ -74,11 +74,11 @@ def make_case(olb, name, n, storage, comp):
     if comp:
         rp = params.tgv_compressible(name, n, 1600.0, 1.0, 0.4)
         sim = olb.Sim((n,) * 3, rp.dx, name, 4, rp.tau, rp.dt, interp_order=4, storage=storage, compressible=True,
-                      gamma=rp.gamma, mu=rp.mu, log_every=10)
+                      gamma=rp.gamma, mu=rp.mu, log_every=10, prandtl=0.75)
         rho, u, th = inputs.ctic3d(n, rp.u0)
         sim.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(th).cuda())
         vs = V.get(name)
-        prm = O.Params(vs, 4, 4, dt=rp.dt, dx=rp.dx, compressible=True, gamma=rp.gamma, mu=rp.mu)
+        prm = O.Params(vs, 4, 4, dt=rp.dt, dx=rp.dx, compressible=True, gamma=rp.gamma, mu=rp.mu, prandtl=0.75)
     else:
         rp = params.tgv_isothermal(name, n, 1600.0, 0.1, 0.4)
         sim = olb.Sim((n,) * 3, rp.dx, name, 2, rp.tau, rp.dt, interp_order=4, storage=storage,

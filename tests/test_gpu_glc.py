@@ -51,6 +51,12 @@ CASES = [
     ("D3Q27", (16, 12, 8), 2, 4, "fp32", False, 0.4, 1.0),
     ("D3Q21", (12, 12, 8), 2, 4, "fp32", False, 0.4, 1.0),
     ("D2Q19", (16, 12), 4, 4, "fp32", True, 0.4, 1.0),
+    # several tiles of the pull (32 x 16 x 16; FP64 32 x 16 x 8; 2D 32 x 32) with ragged tails:
+    # 16-byte staging (n_x a multiple of 16 bytes' elements) and element staging
+    ("D3Q27", (72, 36, 20), 2, 4, "fp32", False, 0.4, 1.0),
+    ("D3Q27", (66, 33, 18), 2, 3, "fp32", False, 0.4, 1.0),
+    ("D3Q27", (40, 34, 18), 2, 2, "fp64", False, 0.4, 1.0),
+    ("D2Q9", (68, 40), 2, 4, "fp64", False, 1.3, 1 / math.sqrt(3)),
 ]
 
 
@@ -68,6 +74,18 @@ def test_one_step_parity_glc(olb, name, shape, N, p, storage, comp, courant, cs)
     slack = 1e-6 if storage != "fp64" else 0.0
     assert abs(red["k"] - diag["k"]) <= (1e-9 + slack) * diag["k"]
     assert abs(red["mass"] - diag["mass"]) <= (1e-12 + slack) * diag["mass"]
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_one_step_parity_glc_prandtl(olb, storage):
+    """The GLC pull with the compressible collision at Pr = 0.75."""
+    sim, prm, state = make_pair(olb, "D3Q45", (16, 16, 12), N=4, p=4, storage=storage, comp=True, prandtl=0.75)
+    sim.set_interpolation("glc")
+    want, _ = glc_steps(prm, state)
+    sim.step(1)
+    got = sim.get_populations(np.zeros_like(state))
+    assert rel_err(got, want, base_of(prm, storage, state.shape[0]), storage) < TOL[storage]
     sim.close()
 
 
