@@ -819,8 +819,6 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
     // The same collision reading the pulled value of plane q of node n from
     // src[q * stride] (a shared-memory chunk: stride = chunk size) where it is
     // used, instead of holding all values in registers (shared-memory staging).
-    // RR: read each value from src where it is used (shared-memory source)
-    // instead of holding all Q of them in registers
     auto collide_from = [&](int n, const C* __restrict__ src, auto STc, auto RED) {
       constexpr int stride = decltype(STc)::value;
       constexpr bool R = decltype(RED)::value;
