@@ -236,6 +236,7 @@ def per_set_table(torch, flush):
     specs.append(dict(WORKLOAD, kernel="generic"))
     specs.append(dict(WORKLOAD, interp="glc"))
     specs.append(dict(WORKLOAD, interp="glc", storage="fp64"))
+    specs.append(dict(WORKLOAD, interp="glc", storage="bf16"))
     specs.append(dict(WORKLOAD, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))

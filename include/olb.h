@@ -270,7 +270,9 @@ int olb_synchronize(olb_handle h, int timeout_ms);
  * step is then two launches (the pull into the second buffer, then the
  * collision), and the global sums stay plain node means.  OLB_EINVAL for
  * another scheme or an axis whose length is not a multiple of p;
- * OLB_EUNSUPPORTED for 16-bit storage or the inflow/outflow x boundary.  While
+ * OLB_EUNSUPPORTED for the inflow/outflow x boundary or departure points too
+ * far for the staged box (a Courant number of several cells).  Every storage;
+ * 16-bit values are interpolated in FP32.  While
  * scheme 1 is set the adjoint calls return OLB_EUNSUPPORTED. */
 int olb_set_interpolation(olb_handle h, int scheme);
 

@@ -1420,8 +1420,6 @@ int olb_set_interpolation(olb_handle h, int scheme) {
     h->glc = 0;
     return OLB_OK;
   }
-  if (h->storage != OLB_FP64 && h->storage != OLB_FP32_SHIFTED)
-    return fail(OLB_EUNSUPPORTED, "the cell-wise GLC pull is built for FP64 and FP32 storage");
   if (h->xbc) return fail(OLB_EUNSUPPORTED, "the cell-wise GLC pull is built for periodic grids only");
   if (h->p > GLC_PMAX) return fail(OLB_EUNSUPPORTED, "GLC order above the built maximum");
   for (int a = 0; a < h->D; ++a)
@@ -1452,7 +1450,7 @@ int olb_set_interpolation(olb_handle h, int scheme) {
   g.b1_elems = 0;
   // x reach rounded to whole 16-byte groups, so that every staged row starts
   // on a 16-byte boundary (the 16-byte staging path)
-  const int VG = 16 / (f64 ? 8 : 4);
+  const int VG = 16 / h->elem;  // stored elements per 16-byte copy
   int exmax = 0;
   for (int i = 0; i < h->Q; ++i) {
     int act = 0, ext[3] = {T[0], T[1], T[2]};
@@ -1486,7 +1484,7 @@ int olb_set_interpolation(olb_handle h, int scheme) {
     exmax = std::max(exmax, ext[0]);
   }
   g.vec16 = (h->grid.n[0] % VG == 0 && exmax % VG == 0 && exmax / VG <= 32) ? 1 : 0;
-  if (glc_smem_bytes(g, f64 ? 8 : 4) > 227 * 1024)
+  if (glc_smem_bytes(g, f64 ? 8 : 4, h->elem) > 227 * 1024)
     return fail(OLB_EUNSUPPORTED, "GLC departure points too far for the staged box (Courant number too large)");
   const size_t bytes = nw * (f64 ? sizeof(double) : sizeof(float));
   if (!h->glc_w) {

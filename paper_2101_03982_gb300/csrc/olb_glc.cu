@@ -71,9 +71,12 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   constexpr int TZ = D == 3 ? GlcTile<C>::TZ : 1;
   constexpr int WS = GLC_PMAX + 1, P1 = P + 1, NW = GT / 32;
   extern __shared__ unsigned char smem_raw[];
+  constexpr bool WIDE = std::is_same<S, C>::value;  // the storage is the arithmetic type
   C* wsm = reinterpret_cast<C*>(smem_raw);  // [3][GLC_PMAX][WS] weights of this velocity
   C* b0 = wsm + 3 * GLC_PMAX * WS;
   C* b1 = b0 + a.box_elems;  // a.b1_elems: the x pass's output
+  // 16-bit storage: the box is staged as stored and converted into b0
+  S* bs = WIDE ? reinterpret_cast<S*>(b0) : reinterpret_cast<S*>(b1 + a.b1_elems);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = (int)(blockIdx.x % (unsigned)a.ntiles);
@@ -98,9 +101,8 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   // round trip, so every copy of the CTA is in flight at once), 16 bytes at a
   // time where the grid allows it, else one element at a time; the row index
   // (yb, zb) advances without a division
-  static_assert(std::is_same<S, C>::value, "the GLC pull stages the storage type as is");
   const S* __restrict__ sp = src + (size_t)plane * a.pad.plane;
-  const unsigned b0s = smem_u32(b0);
+  const unsigned b0s = smem_u32(bs);
   if (a.vec16) {
     // 16-byte copies: the box starts on a 16-byte column (the host rounds the
     // x reach), n0 is a multiple of VG, so a copy never straddles the wrap;
@@ -132,13 +134,18 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
     for (int r = warp; r < ey * ez; r += NW) {
       const S* __restrict__ row = sp + pad_index(a.pad, 0, wrap(y0 - loy + yb, n1), D == 3 ? wrap(z0 - loz + zb, n2) : 0);
       const unsigned drow = b0s + (unsigned)(r * ex * (int)sizeof(S));
-      if (xin) {
-        const S* __restrict__ rx = row + (x0 - lox);
-        for (int xb = lane; xb < ex; xb += 32)
-          cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), rx + xb);
-      } else {
-        for (int xb = lane; xb < ex; xb += 32)
-          cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), row + wrap(x0 - lox + xb, n0));
+      if constexpr (sizeof(S) >= 4) {
+        if (xin) {
+          const S* __restrict__ rx = row + (x0 - lox);
+          for (int xb = lane; xb < ex; xb += 32)
+            cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), rx + xb);
+        } else {
+          for (int xb = lane; xb < ex; xb += 32)
+            cp_async_elem<sizeof(S)>(drow + (unsigned)(xb * (int)sizeof(S)), row + wrap(x0 - lox + xb, n0));
+        }
+      } else {  // 2-byte elements: no asynchronous copy of that size, plain loads
+        (void)drow;
+        for (int xb = lane; xb < ex; xb += 32) bs[r * ex + xb] = row[wrap(x0 - lox + xb, n0)];
       }
       yb += NW;
       while (yb >= ey) {
@@ -149,6 +156,10 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
+  if constexpr (!WIDE) {
+    for (int e = threadIdx.x; e < ex * ey * ez; e += GT) b0[e] = Store<S>::ld(bs[e]);
+    __syncthreads();
+  }
 
   C* cur = b0;
   C* nxt = b1;
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(GT) glc_pull_kernel(const S* __restrict__ src,
 template <typename S>
 int launch_typed(const GlcArgs& a, const void* src, void* dst, void* stream) {
   using C = typename Store<S>::C;
-  const size_t bytes = glc_smem_bytes(a, sizeof(C));
+  const size_t bytes = glc_smem_bytes(a, sizeof(C), sizeof(S));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const unsigned blocks = (unsigned)a.planes * (unsigned)a.ntiles;
   void (*kern)(const S*, S*, const GlcArgs) = nullptr;
@@ -265,15 +276,19 @@ void glc_tile_shape(int D, int elem, int* tx, int* ty, int* tz) {
   *tz = D == 3 ? (f64 ? GlcTile<double>::TZ : GlcTile<float>::TZ) : 1;
 }
 
-size_t glc_smem_bytes(const GlcArgs& a, int elem) {
-  return ((size_t)3 * GLC_PMAX * (GLC_PMAX + 1) + (size_t)a.box_elems + (size_t)a.b1_elems) * (size_t)elem;
+size_t glc_smem_bytes(const GlcArgs& a, int elem, int storage_elem) {
+  size_t b = ((size_t)3 * GLC_PMAX * (GLC_PMAX + 1) + (size_t)a.box_elems + (size_t)a.b1_elems) * (size_t)elem;
+  if (storage_elem != elem) b += ((size_t)a.box_elems * storage_elem + 15) / 16 * 16;  // the box as stored
+  return b;
 }
 
 int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream) {
   switch (storage) {
     case 0: return launch_typed<double>(a, src, dst, stream);
     case 1: return launch_typed<float>(a, src, dst, stream);
-    default: return -1;  // the 16-bit storages are not built for this pull
+    case 2: return launch_typed<__nv_bfloat16>(a, src, dst, stream);
+    case 3: return launch_typed<__half>(a, src, dst, stream);
+    default: return -1;
   }
 }
 

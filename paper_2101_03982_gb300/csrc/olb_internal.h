@@ -186,6 +186,7 @@ struct GlcArgs {
   int box_elems;                    // largest staged box (tile plus reach) over the velocities
   int b1_elems;                     // largest output of the x pass (tile width x box height x box depth)
   int vec16;                        // 1: stage with 16-byte copies (n[0] a multiple of 16 bytes' elements)
+                                    // 16-bit storage: staged as stored, converted to FP32 in shared memory
   int active[MAXQ];                 // bit a: xi_{i,a} != 0
   int first[MAXQ * 3 * GLC_PMAX];   // [i][a][k]
   unsigned char lo[MAXQ * 3], hi[MAXQ * 3];  // [i][a] reach below and above the tile (0 when inactive)
@@ -194,7 +195,8 @@ struct GlcArgs {
 // Tile of the GLC pull for dimension D and element size elem (8: FP64 arithmetic).
 void glc_tile_shape(int D, int elem, int* tx, int* ty, int* tz);
 // Dynamic shared memory of one CTA of the GLC pull (weights and two boxes).
-size_t glc_smem_bytes(const GlcArgs& a, int elem);
+// elem: arithmetic type; storage_elem: the stored type (16-bit storage adds its box).
+size_t glc_smem_bytes(const GlcArgs& a, int elem, int storage_elem);
 // storage 0 (FP64) or 1 (FP32); -1 for a storage not built.  Writes the pulled
 // values of every plane of src into the interior of dst (padded layouts).
 int launch_glc_pull(int storage, const GlcArgs& a, const void* src, void* dst, void* stream);
