@@ -337,6 +337,26 @@ def precision_comp_table(torch, n, steps):
                  fp64_seconds=round(t64, 1))]
 
 
+def precision_shock_table(torch, steps):
+    """The shock-vortex interaction (Sec. 4.1: D2Q19 and D2Q25, N = 4, Mach 1.2
+    standing shock, inflow/outflow x, Pr 0.75) at 1024 x 512 for `steps`
+    steps with k logged every 10 steps, FP32 shifted storage against FP64
+    storage: the largest relative deviation of the k history."""
+    rows = []
+    for name in ("d2q19-comp", "d2q25-comp"):
+        w = WORKLOADS[name]
+        k64, e64 = history_run(dict(w, storage="fp64"), torch, steps, 10)
+        k32, e32 = history_run(dict(w, storage="fp32"), torch, steps, 10)
+        rel = np.abs(k32 - k64) / np.abs(k64)
+        rows.append(dict(velocity_set=w["velocity_set"], compressible=True, Ma=w["Ma"], prandtl=w["prandtl"],
+                         storage="fp32", grid=list(w["shape"]), steps=steps, log_every=10,
+                         k_err_vs_fp64=float(rel.max()),
+                         eps_err_vs_fp64=float((np.abs(e32 - e64) / np.abs(e64)).max()),
+                         k_final=float(k32[-1]), k_final_fp64=float(k64[-1])))
+        torch.cuda.empty_cache()
+    return rows
+
+
 def adjoint_table(torch, configs=((64, "fp32"), (64, "fp64"), (128, "fp32"))):
     """Adjoint of the isothermal step against the forward step (CUDA events).
 
@@ -569,6 +589,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision-steps", type=int, default=2000,
                     help="steps of the FP32/BF16/FP16-vs-FP64 history comparison (0: skip)")
+    ap.add_argument("--precision-shock-steps", type=int, default=4000,
+                    help="steps of the shock-vortex FP32-vs-FP64 k history (0: skip)")
     ap.add_argument("--precision-comp-steps", type=int, default=0,
                     help="steps of the compressible D3Q45 FP32-vs-FP64 k history (0: skip; minutes of FP64)")
     ap.add_argument("--precision-comp-n", type=int, default=128, help="grid of that comparison")
@@ -634,6 +656,8 @@ def main():
     e2e = e2e_measure(w, torch)
     per_set = [] if args.no_per_set else per_set_table(torch, flush)
     precision = [] if args.no_per_set or args.precision_steps <= 0 else precision_table(torch, args.precision_steps)
+    if not args.no_per_set and args.precision_shock_steps > 0:
+        precision += precision_shock_table(torch, args.precision_shock_steps)
     if args.precision_comp_steps > 0:
         precision += precision_comp_table(torch, args.precision_comp_n, args.precision_comp_steps)
     # the histories' deviations beside the throughput of the same set and storage

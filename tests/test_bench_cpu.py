@@ -52,3 +52,11 @@ def test_workload_names_state_the_grid(name):
         assert f"{w['n']}^{dim}" in text
     else:
         assert f"{w['shape'][0]}x{w['shape'][1]}" in text
+
+
+@pytest.mark.parametrize("name", ["d3q45-comp", "d2q19-comp", "d2q25-comp"])
+def test_compressible_workloads_use_the_papers_prandtl_number(name):
+    # Secs. 4.1 and 4.3 run the compressible cases at Pr = 0.75
+    w = bench.WORKLOADS[name]
+    assert w["prandtl"] == 0.75
+    assert "Pr 0.75" in bench.workload_name(w)
