@@ -301,10 +301,11 @@ int olb_set_wait_polls(olb_handle h, long long polls);
  * asynchronous); 0: host pointers (the call completes and checks the device error flag).
  *
  * olb_tape_reserve  allocate nslots tape slots on the device (kept until destroy).  A slot holds
- *                   the pulled populations f~ of one step (Q values per node, adjoint type),
- *                   the input of that step's collision, which is all its adjoint needs.
+ *                   the moments (rho, rho u) of the pulled populations of one step (4 values per
+ *                   node, adjoint type): the transposed collision depends on the state only
+ *                   through them, and the transposed pull on nothing.
  * olb_tape_record   n forward steps of the handle's state (it advances by n steps), step s
- *                   keeping its pulled populations in slot s - 1.  Needs n <= nslots.
+ *                   keeping its pulled moments in slot s - 1.  Needs n <= nslots.
  * olb_tape_adjoint  lambda in: dJ/d(state after the last recorded step); lambda out:
  *                   dJ/d(state n steps earlier), 1 <= n <= recorded steps.  n + 1 launches of
  *                   the adjoint kernel plus one scatter and one gather.

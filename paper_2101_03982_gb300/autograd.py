@@ -13,8 +13,8 @@ torch, with every vector-Jacobian product evaluated by the library's kernels:
   (olb_tape_adjoint); finally the gradient through the initial equilibrium
   (olb_equilibrium_vjp).
 
-Memory: nsteps/every compact checkpoints plus `every` tape slots (the pulled
-populations of one step each).
+Memory: nsteps/every compact checkpoints plus `every` tape slots (four values
+per node each: the moments of one step's pulled populations).
 The recomputation costs one extra forward pass in total.
 """
 import torch

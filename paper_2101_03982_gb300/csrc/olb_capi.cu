@@ -78,8 +78,9 @@ struct olb_ctx {
   std::vector<double> W;      // [Q][3][p+1]
   // adjoint: tape of forward states (padded, like buf) and the adjoint buffers
   std::vector<void*> tape;
-  // slot s: the pulled populations f~ of recorded step s + 1 in the two-phase
-  // kernel's tile order [tile][Q][tile nodes], arithmetic type
+  // slot s: the moments (A = sum of the stored pulled values, j) of recorded
+  // step s + 1, per node in the two-phase kernel's tile order
+  // [tile][4][tile nodes], arithmetic type
   int tape_len = 0;                // slots holding a recorded state
   void* adj[2] = {nullptr, nullptr};
   TmaMaps adj_maps{};              // m[k] of adj[k]
@@ -660,9 +661,9 @@ int adj_prepare(olb_ctx* h) {
 }
 
 // One launch of the adjoint kernel: adjoint input adj[in], output adj[out],
-// pulled forward populations of tape slot `slot` (mode 1; -1 in mode 2).
-// Only the adjoint planes are staged (sched_adj); phase B reads f~ from the
-// slot.
+// moments of the pulled forward populations in tape slot `slot` (mode 1; -1
+// in mode 2).  Only the adjoint planes are staged (sched_adj); phase B reads
+// the moments from the slot.
 int adj_launch(olb_ctx* h, int mode, const std::vector<unsigned char>& st2, int slot, int in, int out) {
   StepLaunch L = base_launch(h);
   L.a.buf[0] = h->adj[in];
@@ -707,10 +708,10 @@ int adjoint_sweep(olb_ctx* h, const std::vector<int>& slots, void* lam_dev) {
   return launch_rc(launch_gather(h->aux, h->adj[cur], lam_dev, h->stream), "adjoint gather");
 }
 
-// Tape slots (after adj_prepare): the pulled populations of one step in the
-// two-phase kernel's tile order.
+// Tape slots (after adj_prepare): the moments of one step's pulled populations
+// in the two-phase kernel's tile order.
 int tape_grow(olb_ctx* h, int nslots) {
-  const size_t bytes = (size_t)h->adj_ntiles * h->Q * h->ainfo.tile * adj_elem(h);
+  const size_t bytes = (size_t)h->adj_ntiles * 4 * h->ainfo.tile * adj_elem(h);
   while ((int)h->tape.size() < nslots) {
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -725,7 +726,8 @@ int tape_grow(olb_ctx* h, int nslots) {
 }
 
 // One forward step of the two-phase kernel from padded buffer `src` (maps
-// `m`) into `dst` that also stores its pulled populations in tape slot `slot`.
+// `m`) into `dst` that also stores the moments of its pulled populations in
+// tape slot `slot`.
 int record_step(olb_ctx* h, void* src, const CUtensorMap* m, void* dst, int slot) {
   StepLaunch L = base_launch(h);
   L.force_generic = 2;

@@ -417,8 +417,10 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
   const int nplan = sched.n[wg];
   S* __restrict__ dst = static_cast<S*>(a.buf[a.src ^ 1]);
   C* __restrict__ scr = static_cast<C*>(a.scratch) + (size_t)blockIdx.x * planes * L::TILE;
-  // a forward step recorded for the adjoint stages the pulled values of tile t
-  // in the tape slab [t][plane][TILE] (kept), the adjoint reads them there
+  // The collision Jacobian of the isothermal step depends on the pulled
+  // populations only through their moments: a recorded forward step keeps, per
+  // tile t, A = sum of the stored pulled values and j = sum xi f~ of every node
+  // in the tape slot [t][4][TILE], and the adjoint reads them there.
   C* const slab = static_cast<C*>(a.slab);
   const unsigned long long keep = policy_evict_last();
 
@@ -507,12 +509,7 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
                       pd.n[2] >= pd.gl[2] + pd.gr[2];
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    if (!ADJ && slab) scr = slab + (size_t)tile * planes * L::TILE;
-    // the pulled forward populations f~ of the tile (adjoint): staged planes
-    // q < Q, or the tape slab of the recorded step
-    const C* __restrict__ fws = (ADJ && slab) ? slab + (size_t)tile * Q * L::TILE : scr;
-    // the tape values of the tile are read by phase B: bring them into L2 now
-    if (ADJ && slab && a.mode == 1 && tid < Q) bulk_prefetch_l2(fws + (size_t)tid * L::TILE, L::TILE * sizeof(C));
+    C* const mom = slab ? slab + (size_t)tile * 4 * L::TILE : nullptr;  // this tile's moments on the tape
     // ---------------- phase A: pull every plane of the tile -----------------
     if constexpr (L::TWOBOX) {
       for (int k = 0; k < nplan && !failed; ++k) {
@@ -851,6 +848,14 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         }
       }
       const C rho = sc.rho_ref + A;
+      if constexpr (!ADJ && !COMP) {
+        if (mom) {  // a recorded step: the moments for the adjoint
+          mom[n] = A;
+          mom[L::TILE + n] = jx;
+          mom[2 * L::TILE + n] = jy;
+          mom[3 * L::TILE + n] = jz;
+        }
+      }
       const C ir = C(1) / rho;
       const C irc = sc.inv_cs / rho;
       const C uhx = uhat_of<COMP>(a, jx, irc, 0), uhy = uhat_of<COMP>(a, jy, irc, 1), uhz = uhat_of<COMP>(a, jz, irc, 2);
@@ -1013,6 +1018,14 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         }
       }
       const C rho = sc.rho_ref + A;
+      if constexpr (!ADJ && !COMP) {
+        if (mom) {  // a recorded step: the moments for the adjoint
+          mom[n] = A;
+          mom[L::TILE + n] = jx;
+          mom[2 * L::TILE + n] = jy;
+          mom[3 * L::TILE + n] = jz;
+        }
+      }
       const C ir = C(1) / rho;
       const C irc = sc.inv_cs / rho;
       const C uhx = uhat_of<COMP>(a, jx, irc, 0), uhy = uhat_of<COMP>(a, jy, irc, 1), uhz = uhat_of<COMP>(a, jz, irc, 2);
@@ -1170,6 +1183,13 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         if (D == 3) jz = fma2(f2(vt.xi[i][2]), f[i], jz);
       }
       const float2 rho = add2(f2(sc.rho_ref), A);
+      if (!ADJ && mom) {  // a recorded step: the moments for the adjoint
+        float* mf = reinterpret_cast<float*>(mom) + n;
+        *reinterpret_cast<float2*>(mf) = A;
+        *reinterpret_cast<float2*>(mf + L::TILE) = jx;
+        *reinterpret_cast<float2*>(mf + 2 * L::TILE) = jy;
+        *reinterpret_cast<float2*>(mf + 3 * L::TILE) = jz;
+      }
       const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
       const float2 uhx = uhat2_of(a, jx, irc, 0), uhy = uhat2_of(a, jy, irc, 1), uhz = uhat2_of(a, jz, irc, 2);
       const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
@@ -1242,6 +1262,13 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         if (D == 3) jz = fma2(f2(vt.xi[i][2]), fi, jz);
       }
       const float2 rho = add2(f2(sc.rho_ref), A);
+      if (!ADJ && mom) {  // a recorded step: the moments for the adjoint
+        float* mf = reinterpret_cast<float*>(mom) + n;
+        *reinterpret_cast<float2*>(mf) = A;
+        *reinterpret_cast<float2*>(mf + L::TILE) = jx;
+        *reinterpret_cast<float2*>(mf + 2 * L::TILE) = jy;
+        *reinterpret_cast<float2*>(mf + 3 * L::TILE) = jz;
+      }
       const float2 irc = make_float2(sc.inv_cs / rho.x, sc.inv_cs / rho.y);
       const float2 uhx = uhat2_of(a, jx, irc, 0), uhy = uhat2_of(a, jy, irc, 1), uhz = uhat2_of(a, jz, irc, 2);
       const float2 q = fma2(uhz, uhz, fma2(uhy, uhy, mul2(uhx, uhx)));
@@ -1337,16 +1364,12 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         }
         return;
       }
-      float2 A = f2(0.f), jx = f2(0.f), jy = f2(0.f), jz = f2(0.f);
-#pragma unroll
-      for (int i = 0; i < QM; ++i) {
-        if (i >= Q) break;
-        const float2 ft = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(fws) + (size_t)i * L::TILE + n);
-        A = add2(A, ft);
-        jx = fma2(f2(vt.xi[i][0]), ft, jx);
-        jy = fma2(f2(vt.xi[i][1]), ft, jy);
-        if (D == 3) jz = fma2(f2(vt.xi[i][2]), ft, jz);
-      }
+      // moments of the pulled forward populations, recorded by the forward step
+      const float* mf = reinterpret_cast<const float*>(mom) + n;
+      const float2 A = *reinterpret_cast<const float2*>(mf);
+      const float2 jx = *reinterpret_cast<const float2*>(mf + L::TILE);
+      const float2 jy = *reinterpret_cast<const float2*>(mf + 2 * L::TILE);
+      const float2 jz = *reinterpret_cast<const float2*>(mf + 3 * L::TILE);
       float2 sig[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) sig[i] = i < Q ? *reinterpret_cast<const float2*>(sg + (size_t)i * L::TILE) : f2(0.f);
@@ -1416,16 +1439,8 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         }
         return;
       }
-      C A = C(0), jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-      for (int i = 0; i < QM; ++i) {
-        if (i >= Q) break;
-        const C ft = fws[(size_t)i * L::TILE + n];
-        A += ft;
-        jx = fma(vt.xi[i][0], ft, jx);
-        jy = fma(vt.xi[i][1], ft, jy);
-        if (D == 3) jz = fma(vt.xi[i][2], ft, jz);
-      }
+      // moments of the pulled forward populations, recorded by the forward step
+      const C A = mom[n], jx = mom[L::TILE + n], jy = mom[2 * L::TILE + n], jz = mom[3 * L::TILE + n];
       C sig[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) sig[i] = i < Q ? sg[(size_t)i * L::TILE] : C(0);
