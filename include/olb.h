@@ -9,13 +9,17 @@
  *   1. pull: every population f_i is interpolated at the departure point
  *      x - xi_i dt (Sec. 3, Eq. sl_streaming) with a tensor product of
  *      equidistant Lagrange polynomials of degree p (one fixed stencil per
- *      velocity, because every node of a uniform grid has the same offset);
+ *      velocity, because every node of a uniform grid has the same offset),
+ *      or with the paper's cell-wise Lagrange elements on Gauss-Lobatto-
+ *      Chebyshev points (olb_set_interpolation);
  *   2. moments rho = sum f_i, rho u = sum xi_i f_i (Sec. 3, Eqs. density and
  *      momentum); compressible runs add 2 rho C_v theta = sum |xi_i-u|^2 f_i/T0
  *      + sum g_i (Sec. 3, temperature relation);
  *   3. Hermite equilibrium of order N (Sec. 3 and Appendix A);
  *   4. BGK relaxation f <- f - (f - f^eq)/tau (Sec. 3, LBE), with
- *      tau = mu/(c_s^2 dt P) + 1/2, P = rho theta, per node when compressible.
+ *      tau = mu/(c_s^2 dt P) + 1/2, P = rho theta, per node when compressible;
+ *      for Pr != 1 the heat flux relaxes at tau_2 through a quasi-equilibrium
+ *      (olb_options.prandtl).
  *
  * Conventions shared by every call
  * --------------------------------
