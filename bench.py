@@ -241,6 +241,8 @@ def per_set_table(torch, flush):
     specs.append(dict(WORKLOAD, n=256))
     specs.append(dict(WORKLOAD, n=256, velocity_set="D3Q45", N=2))
     specs.append(dict(WORKLOADS["d3q45-comp"], n=256))
+    for ma in (0.5, 1.5, 2.0):  # the other Mach numbers of the compressible Taylor-Green runs
+        specs.append(dict(WORKLOADS["d3q45-comp"], n=256, Ma=ma))
     specs.append(dict(WORKLOADS["d3q45-comp"], n=256, prandtl=1.0))  # plain BGK, the cost of the Pr model
     specs.append(dict(WORKLOADS["d3q45-comp"], n=512))  # 99 GB of A/B
     specs.append(WORKLOADS["d2q19-comp"])
@@ -263,7 +265,7 @@ def per_set_table(torch, flush):
         rows.append(dict(kernel=w.get("kernel", "auto"), interp=w.get("interp", "uniform"),
                          velocity_set=w["velocity_set"], grid=w.get("shape") or [w["n"]] * (2 if w["velocity_set"] == "D2Q9" else 3),
                          N=w["N"], p=w["p"], storage=w["storage"], compressible=bool(w.get("compressible")),
-                         prandtl=w.get("prandtl", 1.0),
+                         prandtl=w.get("prandtl", 1.0), Ma=w.get("Ma"),
                          mlups=round(nodes / t / 1e6, 1), ms_per_step=round(t * 1e3, 4),
                          gbs=round(nbytes / t / 1e9, 1), hbm_frac=round(nbytes / t / 1e9 / hbm, 4)))
         if w["storage"] == "fp64":  # bound by the FP64 pipe: % of the measured FP64 FMA peak first
