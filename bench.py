@@ -60,7 +60,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes per launch) of the step kernel for the
 # default workload, from one ncu capture of the kernel source with this hash
 # (summary in profiles/); reported as null once the kernel source changes.
-TRAFFIC = {"kernel_sha": "c76d36bf22ba0f0f", "bytes": 292462592 + 292550144}
+TRAFFIC = {"kernel_sha": "ff4b475166f180ea", "bytes": 292462592 + 292550144}
 
 
 def workload_name(w):

@@ -933,8 +933,13 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         else if (N >= 3) hp = fma(c3, s, c2);
         return fma(fma(hp, s, c1), s, c0);
       };
-      // equilibrium (Appendix A), BGK (Sec. 3) and the stores: f first
+      // equilibrium (Appendix A), BGK (Sec. 3) and the stores: f_i, and in 2D
+      // g_i from the same polynomial value (3D: g in a second loop, the
+      // polynomial evaluated again, which keeps the loop body within the
+      // instruction cache: measured 1% faster there, 3% slower in 2D)
+      constexpr bool GMERGE = COMP && D == 2;
       S* pf = dst + off;
+      const long long gofs = (long long)Q * pd.plane;
       C Pi[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
 #pragma unroll STAGED_UNROLL
       for (int i = 0; i < QM; ++i) {
@@ -947,14 +952,20 @@ __device__ __forceinline__ void wg_body(const StepArgs& a, const VelTab<typename
         C o = ISO32 ? fma(C(1) - sc.inv_tau, fi, vt.wt[i] * eqv) : fma(-fneq, itau, fi);
         if (qe) o = fma(vt.w[i] * (vt.rD[i] - C(2)), qe_dot<D>(vt, i, Fk), o);
         im.put(pf, Store<S>::st(o), pd, off, x, y, z);
+        if constexpr (GMERGE) {
+          const C geqd = vt.w[i] * sc.gfac * fma(rth, ph, gA);
+          const C gi = src[(Q + i) * stride];
+          C og = fma(-(gi - geqd), itau, gi);
+          if (qe) og = fma(vt.w[i], qe_dot<D>(vt, i, Gk), og);
+          im.put(pf + gofs, Store<S>::st(og), pd, off, x, y, z);
+        }
         pf += pd.plane;
         if (R) {
 #pragma unroll
           for (int c = 0; c < 6; ++c) Pi[c] = fma(vt.xx[i][c], fneq, Pi[c]);
         }
       }
-      if (COMP) {
-        // then g, the polynomial evaluated again
+      if constexpr (COMP && !GMERGE) {
 #pragma unroll STAGED_UNROLL
         for (int i = 0; i < QM; ++i) {
           if (i >= Q) break;
