@@ -188,3 +188,38 @@ def test_compressible_adjoint_is_rejected():
     prm = O.Params(vs, 4, 3, dt=0.01, dx=0.1, compressible=True, mu=1e-3)
     with pytest.raises(ValueError):
         A.collide_vjp(prm, np.ones((45, 2)), np.ones((45, 2)))
+
+
+def test_collision_jacobian_depends_on_the_moments_only():
+    """The isothermal collision's Jacobian at f~ depends on f~ only through its
+    moments (rho, j): two pulled states with the same rho and j but different
+    higher moments give the same directional derivative of the forward
+    collision (central differences of the forward oracle, no adjoint code),
+    while a different momentum changes it.  This is why the library's tape
+    keeps four moments per node for the adjoint."""
+    vs = V.get("D3Q27")
+    prm = O.Params(vs, 2, 4, dt=0.05, dx=0.1, tau=0.8)
+    rng = np.random.default_rng(11)
+    M = 6
+    rho = 1.0 + 0.05 * rng.standard_normal(M)
+    u = 0.05 * rng.standard_normal((M, 3))
+    f1 = O.equilibrium(vs, rho, u, np.ones(M), 2) * (1.0 + 0.01 * rng.standard_normal((vs.Q, M)))
+    # a perturbation with no mass and no momentum: project out span{1, xi_a}
+    basis = np.column_stack([np.ones(vs.Q), vs.xi])               # (Q, 4)
+    d = 1e-3 * rng.standard_normal((vs.Q, M))
+    d -= basis @ np.linalg.lstsq(basis, d, rcond=None)[0]
+    f2 = f1 + d
+    assert np.abs(basis.T @ d).max() < 1e-15
+    v = rng.standard_normal((vs.Q, M))
+    sigma = rng.standard_normal((vs.Q, M))
+
+    def dderiv(f, eps=1e-6):
+        plus = O.collide(prm, f + eps * v)[0]
+        minus = O.collide(prm, f - eps * v)[0]
+        return (sigma * (plus - minus) / (2 * eps)).sum(axis=0)
+
+    g1, g2 = dderiv(f1), dderiv(f2)
+    assert np.abs(g1 - g2).max() < 1e-7 * np.abs(g1).max()
+    # control: a change of momentum does change the Jacobian
+    f3 = f1 + 1e-2 * np.outer(vs.xi[:, 0], np.ones(M)) * vs.w[:, None]
+    assert np.abs(dderiv(f3) - g1).max() > 1e-4 * np.abs(g1).max()
